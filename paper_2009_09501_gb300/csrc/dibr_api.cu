@@ -1,0 +1,491 @@
+// dibr_api.cu -- the C-ABI of libdibr (declared in include/dibr.h): contexts, argument
+// checks, the depth-to-shift tables of Fig. 3, TMA descriptors, staging of host
+// buffers, and the launches of the fused kernels.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dibr.h"
+#include "dibr_context.h"
+#include "dibr_internal.h"
+
+using namespace dibr;
+
+// ------------------------------------------------------------------------ helpers
+void dibr_ctx::set_error(const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> g(err_mu);
+  last_error = buf;
+}
+
+dibr_status dibr_ctx::cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return DIBR_E_CUDA;
+}
+
+void *dibr_ctx::dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (alloc_hook) return alloc_hook(bytes, alloc_user);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dibr_ctx::dev_free(void *p) {
+  if (!p) return;
+  if (free_hook) free_hook(p, alloc_user);
+  else cudaFreeAsync(p, stream);
+}
+
+dibr_status dibr_ctx::ensure(DevBuf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.ptr) return DIBR_OK;
+  if (b.ptr) {
+    cudaStreamSynchronize(stream);
+    dev_free(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  b.ptr = static_cast<uint8_t *>(dev_alloc(bytes));
+  if (!b.ptr) {
+    set_error("device allocation of %zu bytes failed", bytes);
+    return DIBR_E_NOMEM;
+  }
+  b.bytes = bytes;
+  return DIBR_OK;
+}
+
+// ------------------------------------------------------------- parameter checking
+static bool valid_enum(int v, int lo, int hi) { return v >= lo && v <= hi; }
+
+static dibr_status check_params(const dibr_params *p, const dibr_image *img, std::string *why) {
+  if (!p) { *why = "params is NULL"; return DIBR_E_INVALID; }
+  if (!valid_enum(p->depth_rule, 0, 2)) { *why = "unknown depth_rule"; return DIBR_E_INVALID; }
+  if (!valid_enum(p->disparity_rule, 0, 1)) { *why = "unknown disparity_rule"; return DIBR_E_INVALID; }
+  if (!valid_enum(p->warp_mode, 0, 1)) { *why = "unknown warp_mode"; return DIBR_E_INVALID; }
+  if (p->warp_mode == DIBR_WARP_GATHER_FIG3 && p->disparity_rule != DIBR_DISP_PAPER) {
+    *why = "the Fig. 3 gather mode is defined for the paper's disparity rule only";
+    return DIBR_E_INVALID;
+  }
+  if (p->max_parallax_px < 0 || p->max_parallax_px > 1024) { *why = "max_parallax_px outside 0..1024"; return DIBR_E_INVALID; }
+  if (p->threshold < 0 || p->threshold > 255) { *why = "threshold outside 0..255"; return DIBR_E_INVALID; }
+  if (p->depth_rule == DIBR_DEPTH_LUMA_XBF) {
+    if (!(p->xbf_sigma_s > 0.f) || !(p->xbf_sigma_r > 0.f) || p->xbf_radius < 1 || p->xbf_radius > 8) {
+      *why = "cross-bilateral parameters out of range (sigmas > 0, radius 1..8)";
+      return DIBR_E_INVALID;
+    }
+  }
+  const uint32_t all = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS | DIBR_OUT_DEPTH;
+  if (p->outputs == 0 || (p->outputs & ~all)) { *why = "outputs must be a non-empty set of DIBR_OUT_* bits"; return DIBR_E_INVALID; }
+  if (img) {
+    if (img->width < 1 || img->height < 1 || img->width > kMaxWidth || img->height > 65535) {
+      *why = "image size outside 1..7680 x 1..65535";
+      return DIBR_E_INVALID;
+    }
+    if (!img->rgb) { *why = "image pointer is NULL"; return DIBR_E_INVALID; }
+    if (img->pitch < 3 * static_cast<int64_t>(img->width)) { *why = "pitch < 3*width"; return DIBR_E_INVALID; }
+    if ((p->outputs & DIBR_OUT_HSBS) && (img->width & 1)) { *why = "HSBS needs an even width"; return DIBR_E_INVALID; }
+  }
+  return DIBR_OK;
+}
+
+static dibr_status check_outputs(const dibr_params *p, const dibr_image *img, const dibr_outputs *o,
+                                 std::string *why) {
+  if (!o) { *why = "outputs is NULL"; return DIBR_E_INVALID; }
+  const uint8_t *ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
+  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  bool rgb_out = false;
+  for (int i = 0; i < O_COUNT; ++i) {
+    if ((p->outputs & bits[i]) && !ptrs[i]) { *why = "a requested output pointer is NULL"; return DIBR_E_INVALID; }
+    if ((p->outputs & bits[i]) && i != O_DEPTH) rgb_out = true;
+  }
+  if (rgb_out && o->pitch < 3 * static_cast<int64_t>(img->width)) { *why = "output pitch < 3*width"; return DIBR_E_INVALID; }
+  if ((p->outputs & DIBR_OUT_DEPTH) && o->depth_pitch < img->width) { *why = "depth_pitch < width"; return DIBR_E_INVALID; }
+  return DIBR_OK;
+}
+
+// ----------------------------------------------------- depth -> shift tables (Fig. 3)
+static int64_t floor_div510(int64_t a) {  // floor(a / 510)
+  int64_t q = a / 510;
+  if (a % 510 != 0 && a < 0) --q;
+  return q;
+}
+
+// Fig. 3: s_L(d) = -(P/2) d/255 (d > T) or (P/2)(1 - d/255); numerator over 510.
+static int64_t shift_num510(int d, int P, int T) {
+  return d > T ? -static_cast<int64_t>(P) * d : static_cast<int64_t>(P) * (255 - d);
+}
+
+static void build_tables(const dibr_params *p, int16_t *hL, int16_t *hR, int32_t *num) {
+  for (int d = 0; d < 256; ++d) {
+    if (p->disparity_rule == DIBR_DISP_PAPER) {
+      const int64_t n = shift_num510(d, p->max_parallax_px, p->threshold);
+      hL[d] = static_cast<int16_t>(floor_div510(n));
+      hR[d] = static_cast<int16_t>(floor_div510(-n));
+      if (num) num[d] = static_cast<int32_t>(n);
+    } else {
+      const int64_t m = static_cast<int64_t>(p->max_parallax_px) * d / 510;
+      hL[d] = static_cast<int16_t>(-m);
+      hR[d] = static_cast<int16_t>(m);
+      if (num) num[d] = static_cast<int32_t>(-510 * m);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launch planning
+static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, BandArgs &a, int &smem) {
+  a.W = W;
+  a.H = H;
+  a.nch = (W + kChunk - 1) / kChunk;
+  a.nc = std::min(kMaxConsumers, round_up(a.nch, 32));
+  a.nbox = (3 * W + kBoxBytes - 1) / kBoxBytes;
+  a.srow = round_up(std::max(a.nbox * kBoxBytes, 48 * a.nch), 128);
+  a.ystride = a.nch * kChunk;
+  a.depth_src = depth_src;
+  const int min_nb = depth_src == DS_BINOM5 ? 5 : 2;
+  int nb = kMaxRing;
+  if (tune_ring > 0) nb = std::min(nb, tune_ring);
+  while (nb > min_nb && band_smem_layout(nb, a.srow, a.ystride, a.nch, depth_src).total > max_smem) --nb;
+  const BandSmem L = band_smem_layout(nb, a.srow, a.ystride, a.nch, depth_src);
+  if (L.total > max_smem) {
+    set_error("width %d needs %d bytes of shared memory (limit %d)", W, L.total, max_smem);
+    return DIBR_E_INVALID;
+  }
+  a.nb = nb;
+  smem = L.total;
+  int per_sm = std::max(1, (smem_per_sm) / (L.total + 1024));
+  per_sm = std::min(per_sm, std::max(1, 2048 / (a.nc + 32)));
+  if (tune_ctas_per_sm > 0) per_sm = std::min(per_sm, tune_ctas_per_sm);
+  a.grid = std::max(1, std::min(H, num_sms * per_sm));
+  a.status = status_dev;
+  a.timeout_ns = timeout_ns;
+  return DIBR_OK;
+}
+
+dibr_status dibr_ctx::encode_input(BandArgs &a, const uint8_t *dev_rgb, int64_t pitch) {
+  auto enc = get_encoder();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is unavailable");
+    return DIBR_E_CUDA;
+  }
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(3) * a.W, static_cast<cuuint64_t>(a.H)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxBytes), 1u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(dev_rgb), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return DIBR_E_CUDA;
+  }
+  return DIBR_OK;
+}
+
+static bool tma_ok(const uint8_t *p, int64_t pitch) {
+  return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (pitch & 15) == 0;
+}
+
+// Enqueues the whole pipeline for one image whose input and outputs are in device memory.
+dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o) {
+  const int W = img->width, H = img->height;
+  const uint8_t *in = img->rgb;
+  int64_t pitch = img->pitch;
+  if (!tma_ok(in, pitch)) {
+    // TMA needs a 16-byte aligned base and pitch: repack into an aligned device buffer
+    const int64_t ap = round_up(3 * W, 16);
+    dibr_status s = ensure(realign, static_cast<size_t>(ap) * H);
+    if (s != DIBR_OK) return s;
+    cudaError_t e = cudaMemcpy2DAsync(realign.ptr, ap, in, pitch, 3 * static_cast<size_t>(W), H,
+                                      cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "repacking the input");
+    in = realign.ptr;
+    pitch = ap;
+  }
+  int depth_src = p->depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5
+                  : p->depth_rule == DIBR_DEPTH_LUMA     ? DS_LUMA
+                                                         : DS_GLOBAL;
+  BandArgs &a = args;
+  int smem = 0;
+  dibr_status s = plan_band(W, H, depth_src, a, smem);
+  if (s != DIBR_OK) return s;
+  if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
+  if (depth_src == DS_GLOBAL) {
+    const int64_t dp = round_up(W, 16);
+    if ((s = ensure(xbf_depth, static_cast<size_t>(dp) * H)) != DIBR_OK) return s;
+    cudaError_t e = launch_xbf(in, pitch, W, H, p->xbf_radius, p->xbf_sigma_s, p->xbf_sigma_r,
+                               xbf_depth.ptr, dp, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cross-bilateral launch");
+    a.depth_in = xbf_depth.ptr;
+    a.depth_in_pitch = dp;
+  } else {
+    a.depth_in = nullptr;
+    a.depth_in_pitch = 0;
+  }
+  a.out[O_ANA] = o->anaglyph;
+  a.out[O_LEFT] = o->left;
+  a.out[O_RIGHT] = o->right;
+  a.out[O_HSBS] = o->hsbs;
+  a.out[O_DEPTH] = o->depth;
+  a.out_pitch = o->pitch;
+  a.depth_pitch = o->depth_pitch;
+  a.outputs = p->outputs;
+  a.warp_mode = p->warp_mode;
+  int16_t hL[256], hR[256];
+  build_tables(p, hL, hR, a.lut_n);
+  for (int d = 0; d < 256; ++d)
+    a.lut_h[d] = static_cast<int32_t>((static_cast<uint32_t>(static_cast<uint16_t>(hR[d])) << 16) |
+                                      static_cast<uint16_t>(hL[d]));
+  cudaError_t e = launch_band(a, smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
+  ++launches;
+  return DIBR_OK;
+}
+
+dibr_status dibr_ctx::read_status() {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, status_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "synchronising the context stream");
+  if (st) {
+    cudaMemsetAsync(status_dev, 0, sizeof(int), stream);
+    cudaStreamSynchronize(stream);
+    set_error("a bounded device-side wait gave up (status 0x%x)", st);
+    return DIBR_E_TIMEOUT;
+  }
+  return DIBR_OK;
+}
+
+// ------------------------------------------------------------------- the C-ABI
+extern "C" {
+
+dibr_status dibr_params_default(dibr_params *p) {
+  if (!p) return DIBR_E_INVALID;
+  p->depth_rule = DIBR_DEPTH_LUMA_BINOM5;
+  p->disparity_rule = DIBR_DISP_PAPER;
+  p->warp_mode = DIBR_WARP_FORWARD;
+  p->max_parallax_px = 16;
+  p->threshold = 150;
+  p->xbf_sigma_s = 1.5f;
+  p->xbf_sigma_r = 16.0f;
+  p->xbf_radius = 2;
+  p->outputs = DIBR_OUT_ANAGLYPH;
+  return DIBR_OK;
+}
+
+dibr_status dibr_validate(const dibr_params *p, const dibr_image *img) {
+  std::string why;
+  return check_params(p, img, &why);
+}
+
+dibr_status dibr_shift_tables(const dibr_params *p, int16_t hL[256], int16_t hR[256]) {
+  std::string why;
+  dibr_status s = check_params(p, nullptr, &why);
+  if (s != DIBR_OK) return s;
+  if (!hL || !hR) return DIBR_E_INVALID;
+  build_tables(p, hL, hR, nullptr);
+  return DIBR_OK;
+}
+
+dibr_status dibr_create(const dibr_config *cfg_in, dibr_ctx **out) {
+  if (!out) return DIBR_E_INVALID;
+  *out = nullptr;
+  dibr_config cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  if (cfg_in) cfg = *cfg_in;
+  if ((cfg.alloc == nullptr) != (cfg.free == nullptr)) return DIBR_E_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return DIBR_E_CUDA;
+  }
+  if (cfg.device < 0 || cfg.device >= ndev) return DIBR_E_INVALID;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, cfg.device) != cudaSuccess) return DIBR_E_CUDA;
+  if (!(prop.major == 10 && prop.minor == 3)) return DIBR_E_CUDA;  // built for sm_103a only
+  if (cudaSetDevice(cfg.device) != cudaSuccess) return DIBR_E_CUDA;
+  dibr_ctx *c = new dibr_ctx();
+  c->device = cfg.device;
+  c->num_sms = prop.multiProcessorCount;
+  c->max_smem = static_cast<int>(prop.sharedMemPerBlockOptin);
+  c->smem_per_sm = static_cast<int>(prop.sharedMemPerMultiprocessor);
+  c->alloc_hook = cfg.alloc;
+  c->free_hook = cfg.free;
+  c->alloc_user = cfg.user;
+  c->mem_budget = cfg.mem_budget_bytes;
+  c->max_streams = cfg.max_streams > 0 ? cfg.max_streams : 64;
+  c->max_batch = cfg.max_batch > 0 ? cfg.max_batch : 256;
+  if (cfg.cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cfg.cuda_stream);
+    c->owns_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return DIBR_E_CUDA;
+    }
+    c->owns_stream = true;
+  }
+  c->status_dev = static_cast<int *>(c->dev_alloc(64));
+  if (!c->status_dev) {
+    if (c->owns_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return DIBR_E_NOMEM;
+  }
+  cudaMemsetAsync(c->status_dev, 0, 64, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    c->dev_free(c->status_dev);
+    if (c->owns_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return DIBR_E_CUDA;
+  }
+  *out = c;
+  return DIBR_OK;
+}
+
+void dibr_destroy(dibr_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  c->shutdown_serving();
+  cudaStreamSynchronize(c->stream);
+  c->release_buffers();
+  c->dev_free(c->status_dev);
+  cudaStreamSynchronize(c->stream);
+  if (c->owns_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char *dibr_last_error(dibr_ctx *c) {
+  if (!c) return "null context";
+  std::lock_guard<std::mutex> g(c->err_mu);
+  c->last_error_copy = c->last_error;
+  return c->last_error_copy.c_str();
+}
+
+void *dibr_stream(dibr_ctx *c) { return c ? static_cast<void *>(c->stream) : nullptr; }
+
+dibr_status dibr_enqueue_image(dibr_ctx *c, const dibr_image *img, const dibr_params *p,
+                               const dibr_outputs *o) {
+  if (!c || !img) return DIBR_E_INVALID;
+  std::string why;
+  dibr_status s = check_params(p, img, &why);
+  if (s == DIBR_OK) s = check_outputs(p, img, o, &why);
+  if (s != DIBR_OK) {
+    c->set_error("%s", why.c_str());
+    return s;
+  }
+  if (!img->on_device || !o->on_device) {
+    c->set_error("dibr_enqueue_image needs device buffers");
+    return DIBR_E_INVALID;
+  }
+  cudaSetDevice(c->device);
+  return c->enqueue_device(img, p, o);
+}
+
+dibr_status dibr_synchronize(dibr_ctx *c) {
+  if (!c) return DIBR_E_INVALID;
+  cudaSetDevice(c->device);
+  return c->read_status();
+}
+
+dibr_status dibr_synthesize_image(dibr_ctx *c, const dibr_image *img, const dibr_params *p,
+                                  const dibr_outputs *o) {
+  if (!c || !img) return DIBR_E_INVALID;
+  std::string why;
+  dibr_status s = check_params(p, img, &why);
+  if (s == DIBR_OK) s = check_outputs(p, img, o, &why);
+  if (s != DIBR_OK) {
+    c->set_error("%s", why.c_str());
+    return s;
+  }
+  cudaSetDevice(c->device);
+  return c->synthesize_staged(img, p, o);
+}
+
+}  // extern "C"
+
+// Blocking single-frame path: host buffers are staged through context-owned device
+// memory (input H2D, outputs D2H) on the context's stream.
+dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o) {
+  const int W = img->width, H = img->height;
+  dibr_image din = *img;
+  dibr_outputs dout = *o;
+  cudaError_t e;
+  dibr_status s;
+  if (!img->on_device) {
+    const int64_t ap = round_up(3 * W, 16);
+    if ((s = ensure(stage_in, static_cast<size_t>(ap) * H)) != DIBR_OK) return s;
+    e = cudaMemcpy2DAsync(stage_in.ptr, ap, img->rgb, img->pitch, 3 * static_cast<size_t>(W), H,
+                          cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "input upload");
+    din.rgb = stage_in.ptr;
+    din.pitch = ap;
+    din.on_device = 1;
+  }
+  uint8_t *host_ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
+  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  const int64_t op = round_up(3 * W, 16), dp = round_up(W, 16);
+  if (!o->on_device) {
+    size_t total = 0;
+    size_t offs[O_COUNT];
+    for (int i = 0; i < O_COUNT; ++i) {
+      offs[i] = total;
+      if (p->outputs & bits[i]) total += static_cast<size_t>(i == O_DEPTH ? dp : op) * H;
+    }
+    if ((s = ensure(stage_out, total)) != DIBR_OK) return s;
+    uint8_t **dptr[O_COUNT] = {&dout.anaglyph, &dout.left, &dout.right, &dout.hsbs, &dout.depth};
+    for (int i = 0; i < O_COUNT; ++i) *dptr[i] = (p->outputs & bits[i]) ? stage_out.ptr + offs[i] : nullptr;
+    dout.pitch = op;
+    dout.depth_pitch = dp;
+    dout.on_device = 1;
+  }
+  if ((s = enqueue_device(&din, p, &dout)) != DIBR_OK) return s;
+  if (!o->on_device) {
+    uint8_t *dptrs[O_COUNT] = {dout.anaglyph, dout.left, dout.right, dout.hsbs, dout.depth};
+    for (int i = 0; i < O_COUNT; ++i) {
+      if (!(p->outputs & bits[i])) continue;
+      const bool dep = i == O_DEPTH;
+      e = cudaMemcpy2DAsync(host_ptrs[i], dep ? o->depth_pitch : o->pitch, dptrs[i], dep ? dp : op,
+                            dep ? static_cast<size_t>(W) : 3 * static_cast<size_t>(W), H,
+                            cudaMemcpyDeviceToHost, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "output download");
+    }
+  }
+  return read_status();
+}
+
+void dibr_ctx::release_buffers() {
+  for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth}) {
+    dev_free(b->ptr);
+    b->ptr = nullptr;
+    b->bytes = 0;
+  }
+  release_batch_buffers();
+}

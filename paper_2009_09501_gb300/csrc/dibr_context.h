@@ -1,0 +1,71 @@
+// dibr_context.h -- the library context behind the opaque dibr_ctx handle.
+#pragma once
+
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dibr.h"
+#include "dibr_internal.h"
+
+namespace dibr {
+
+struct DevBuf {
+  uint8_t *ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct ServeState;  // dibr_serve.cu
+
+}  // namespace dibr
+
+struct dibr_ctx {
+  int device = 0;
+  int num_sms = 1;
+  int max_smem = 0;
+  int smem_per_sm = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_stream = false;
+  void *(*alloc_hook)(size_t, void *) = nullptr;
+  void (*free_hook)(void *, void *) = nullptr;
+  void *alloc_user = nullptr;
+  uint64_t mem_budget = 0;
+  int max_streams = 64;
+  int max_batch = 256;
+  int *status_dev = nullptr;
+  unsigned long long timeout_ns = 2000000000ull;  // 2 s per bounded device-side wait
+  int tune_ring = 0;         // 0: as many ring slots as shared memory allows
+  int tune_ctas_per_sm = 0;  // 0: as many as fit
+  uint64_t launches = 0;     // kernels launched by this context
+
+  std::mutex err_mu;
+  std::string last_error, last_error_copy;
+
+  dibr::DevBuf stage_in, stage_out, realign, xbf_depth;
+  dibr::BandArgs args;  // scratch for one launch (large: keeps it off the stack)
+
+  // batched launches (dibr_batch.cu)
+  dibr::DevBuf batch_desc, batch_img, batch_depth;
+  std::vector<uint8_t> batch_host;
+
+  // serving loop (dibr_serve.cu)
+  dibr::ServeState *serve = nullptr;
+
+  void set_error(const char *fmt, ...);
+  dibr_status cuda_fail(cudaError_t e, const char *what);
+  void *dev_alloc(size_t bytes);
+  void dev_free(void *p);
+  dibr_status ensure(dibr::DevBuf &b, size_t bytes);
+  dibr_status plan_band(int W, int H, int depth_src, dibr::BandArgs &a, int &smem);
+  dibr_status encode_input(dibr::BandArgs &a, const uint8_t *dev_rgb, int64_t pitch);
+  dibr_status enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
+  dibr_status synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
+  dibr_status read_status();
+  void release_buffers();
+  void release_batch_buffers();
+  void shutdown_serving();
+};
