@@ -203,7 +203,9 @@ def run_ours(args):
 
     img = scenes.config_scene(2)
     H, W = img.shape[:2]
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library runs on it and the CUDA events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = D.Context(device=local, stream=stream.cuda_stream)
     p = D.make_params(max_parallax=P4K, outputs=OUTPUTS)
 

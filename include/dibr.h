@@ -187,6 +187,25 @@ dibr_status dibr_synthesize_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
 dibr_status dibr_enqueue_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
                                const dibr_params *p, int n_params, const dibr_outputs *outs);
 
+/* Launch tuning: the knobs an autotuner sweeps (the paper has no counterpart; these
+ * change speed, never results).  A zero field means "automatic".
+ *   ring_slots     input rows staged in shared memory per CTA, 4..8;
+ *   ctas_per_sm    CTAs resident per SM at most;
+ *   load_mode      1: one bulk copy per input row; 2/3/4: 3-D tensor boxes whose inner
+ *                  rows are 16 / 128 / 256 bytes; 5: 2-D tensor boxes of 256 bytes.
+ *                  A mode that does not fit an image's width or alignment falls back to
+ *                  mode 5, which fits every image;
+ *   l2_prefetch    1: each CTA prefetches its later input rows into L2 at launch;
+ *                  2: it does not;
+ *   rows_per_unit  rows per work unit of a batched launch (dibr_synthesize_batch).
+ * dibr_set_tuning() rejects out-of-range values with DIBR_E_INVALID. */
+typedef struct {
+    int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit;
+} dibr_tuning;
+
+dibr_status dibr_set_tuning(dibr_ctx *ctx, const dibr_tuning *t);
+dibr_status dibr_get_tuning(dibr_ctx *ctx, dibr_tuning *t);
+
 /* ------------------------------------------------------------------ serving loop ---
  * Concurrent video streams with continuous batching: frames submitted on any open
  * stream are gathered by a scheduler thread, copied to per-stream device buffers on a

@@ -161,29 +161,74 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
-dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, BandArgs &a, int &smem) {
+dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, BandArgs &a,
+                               int &smem, int &per_sm) {
   a.W = W;
   a.H = H;
   a.nch = (W + kChunk - 1) / kChunk;
-  a.nc = std::min(kMaxConsumers, round_up(a.nch, 32));
-  a.nbox = (3 * W + kBoxBytes - 1) / kBoxBytes;
-  a.srow = round_up(std::max(a.nbox * kBoxBytes, 48 * a.nch), 128);
-  a.ystride = a.nch * kChunk;
+  a.nc = round_up(a.nch, 32);  // one 16-pixel chunk per consumer thread
+  // how rows reach shared memory: the tuned mode when the image allows it, else the
+  // automatic choice (one bulk copy per row when rows are whole 16-byte units)
+  const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15u) == 0 && (pitch & 15) == 0;
+  int mode = tuning.load_mode;
+  const int row = 3 * W;
+  auto fits = [&](int m) {
+    if (m == 1) return aligned && row % 16 == 0;
+    if (m == 2) return aligned && row % 16 == 0;
+    if (m == 3) return aligned && row % 128 == 0;
+    if (m == 4) return aligned && row % 256 == 0;
+    return m == 5;
+  };
+  if (mode == 0) mode = fits(1) ? 1 : 5;
+  if (!fits(mode)) mode = 5;
+  a.row_bytes = row;
+  a.in = in;
+  a.in_pitch = pitch;
+  if (mode == 1) {
+    a.load_mode = LM_BULK;
+    a.nbox = 1;
+    a.box_bytes = row;
+    a.box_step = 0;
+  } else if (mode <= 4) {
+    const int inner = mode == 2 ? 16 : mode == 3 ? 128 : 256;
+    const int n = row / inner;
+    a.load_mode = LM_T3;
+    a.tinner = inner;
+    a.nbox = (n + 255) / 256;
+    a.box_step = round_up((n + a.nbox - 1) / a.nbox, inner >= 128 ? 1 : 128 / inner);  // 128-byte aligned boxes
+    a.box_bytes = inner * a.box_step;
+  } else {
+    a.load_mode = LM_T2;
+    a.nbox = (row + kBoxBytes - 1) / kBoxBytes;
+    a.box_step = kBoxBytes;
+    a.box_bytes = kBoxBytes;
+  }
+  a.l2_prefetch = tuning.l2_prefetch == 1 ? 1 : 0;
+  a.srow = round_up(std::max(a.nbox * a.box_bytes, 48 * a.nch), 128);
   a.depth_src = depth_src;
-  const int min_nb = depth_src == DS_BINOM5 ? 5 : 2;
-  int nb = kMaxRing;
-  if (tune_ring > 0) nb = std::min(nb, tune_ring);
-  while (nb > min_nb && band_smem_layout(nb, a.srow, a.ystride, a.nch, depth_src).total > max_smem) --nb;
-  const BandSmem L = band_smem_layout(nb, a.srow, a.ystride, a.nch, depth_src);
-  if (L.total > max_smem) {
-    set_error("width %d needs %d bytes of shared memory (limit %d)", W, L.total, max_smem);
+  const int min_nb = depth_src == DS_BINOM5 ? 4 : 2;
+  const int max_nb = tuning.ring_slots > 0 ? std::max(min_nb, std::min(kMaxRing, tuning.ring_slots)) : kMaxRing;
+  // at most 128 registers per thread (the kernel's launch bound) and 2048 threads per SM
+  const int max_per = std::max(1, std::min(65536 / (a.nc * 128), 2048 / a.nc));
+  auto per_for = [&](int nb) {
+    const int tot = band_smem_layout(nb, a.srow, a.nch, depth_src).total;
+    if (tot > max_smem) return 0;
+    int per = std::min(max_per, smem_per_sm / (tot + 1024));
+    if (tuning.ctas_per_sm > 0) per = std::min(per, tuning.ctas_per_sm);
+    return per;
+  };
+  int best = 0;
+  for (int nb = min_nb; nb <= max_nb; ++nb) best = std::max(best, per_for(nb));
+  if (best < 1) {
+    set_error("width %d needs more shared memory than the device offers", W);
     return DIBR_E_INVALID;
   }
+  int nb = min_nb;
+  for (int k = min_nb; k <= max_nb; ++k)
+    if (per_for(k) == best) nb = k;
   a.nb = nb;
-  smem = L.total;
-  int per_sm = std::max(1, (smem_per_sm) / (L.total + 1024));
-  per_sm = std::min(per_sm, std::max(1, 2048 / (a.nc + 32)));
-  if (tune_ctas_per_sm > 0) per_sm = std::min(per_sm, tune_ctas_per_sm);
+  smem = band_smem_layout(nb, a.srow, a.nch, depth_src).total;
+  per_sm = best;
   a.grid = std::max(1, std::min(H, num_sms * per_sm));
   a.status = status_dev;
   a.timeout_ns = timeout_ns;
@@ -196,13 +241,26 @@ dibr_status dibr_ctx::encode_input(BandArgs &a, const uint8_t *dev_rgb, int64_t 
     set_error("cuTensorMapEncodeTiled is unavailable");
     return DIBR_E_CUDA;
   }
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(3) * a.W, static_cast<cuuint64_t>(a.H)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxBytes), 1u};
-  cuuint32_t estr[2] = {1u, 1u};
-  CUresult r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(dev_rgb), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (a.load_mode == LM_BULK) return DIBR_OK;  // no tensor map needed
+  CUresult r;
+  if (a.load_mode == LM_T3) {
+    const cuuint64_t inner = static_cast<cuuint64_t>(a.tinner);
+    cuuint64_t dims[3] = {inner, static_cast<cuuint64_t>(3) * a.W / inner, static_cast<cuuint64_t>(a.H)};
+    cuuint64_t strides[2] = {inner, static_cast<cuuint64_t>(pitch)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(inner), static_cast<cuuint32_t>(a.box_step), 1u};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(dev_rgb), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(3) * a.W, static_cast<cuuint64_t>(a.H)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(kBoxBytes), 1u};
+    cuuint32_t estr[2] = {1u, 1u};
+    r = enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(dev_rgb), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
     return DIBR_E_CUDA;
@@ -234,8 +292,8 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
                   : p->depth_rule == DIBR_DEPTH_LUMA     ? DS_LUMA
                                                          : DS_GLOBAL;
   BandArgs &a = args;
-  int smem = 0;
-  dibr_status s = plan_band(W, H, depth_src, a, smem);
+  int smem = 0, per_sm = 1;
+  dibr_status s = plan_band(W, H, depth_src, in, pitch, a, smem, per_sm);
   if (s != DIBR_OK) return s;
   if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
   if (depth_src == DS_GLOBAL) {
@@ -264,7 +322,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   for (int d = 0; d < 256; ++d)
     a.lut_h[d] = static_cast<int32_t>((static_cast<uint32_t>(static_cast<uint16_t>(hR[d])) << 16) |
                                       static_cast<uint16_t>(hL[d]));
-  cudaError_t e = launch_band(a, smem, stream);
+  cudaError_t e = launch_band(a, smem, per_sm, stream);
   if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
   ++launches;
   return DIBR_OK;
@@ -390,6 +448,24 @@ const char *dibr_last_error(dibr_ctx *c) {
 }
 
 void *dibr_stream(dibr_ctx *c) { return c ? static_cast<void *>(c->stream) : nullptr; }
+
+dibr_status dibr_set_tuning(dibr_ctx *c, const dibr_tuning *t) {
+  if (!c || !t) return DIBR_E_INVALID;
+  if (t->ring_slots < 0 || t->ring_slots > kMaxRing || (t->ring_slots > 0 && t->ring_slots < 2) ||
+      t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || t->load_mode < 0 || t->load_mode > 5 ||
+      t->l2_prefetch < 0 || t->l2_prefetch > 2 || t->rows_per_unit < 0 || t->rows_per_unit > 4096) {
+    c->set_error("tuning value out of range");
+    return DIBR_E_INVALID;
+  }
+  c->tuning = *t;
+  return DIBR_OK;
+}
+
+dibr_status dibr_get_tuning(dibr_ctx *c, dibr_tuning *t) {
+  if (!c || !t) return DIBR_E_INVALID;
+  *t = c->tuning;
+  return DIBR_OK;
+}
 
 dibr_status dibr_enqueue_image(dibr_ctx *c, const dibr_image *img, const dibr_params *p,
                                const dibr_outputs *o) {

@@ -6,13 +6,26 @@
 //   of the left and right views with occlusion -> row-local hole fill (inpainting) ->
 //   stereo formatting (anaglyph, L/R pair, half side-by-side, depth).
 // Nothing but the input and the requested outputs touches HBM: luminance, depth, the
-// z-buffers and the shift tables live in shared memory and registers.
+// z-buffers and the shift tables live in registers and shared memory.
 //
-// Warp roles: warps 0..nc/32-1 are consumers (each thread owns 16-pixel chunks of a
-// row); the last warp is the producer, which streams input rows into a ring of
-// shared-memory slots with 2-D TMA tensor loads (cp.async.bulk.tensor), completion
-// tracked by mbarriers.  Every wait is bounded (%globaltimer); a wait that gives up sets
-// a bit of the status word and the CTA unwinds.
+// Thread c owns the 16 columns 16c .. 16c+15 of every row.  Input rows stream into a
+// ring of shared-memory slots with 2-D TMA tensor loads (cp.async.bulk.tensor), each
+// slot's completion tracked by an mbarrier; warp 0 refills a slot right after the row
+// barrier that proves every thread is done with it.  Every wait is bounded
+// (%globaltimer); a wait that gives up sets a bit of the status word and the CTA
+// unwinds after letting its own copies land.
+//
+// Per consumer thread and row y:
+//   A  luminance of row y+2 for its 16 columns plus 2 on each side, fed into a cascade
+//      of four [1 1] row sums held in registers, which yields the vertical binomial of
+//      row y; the horizontal binomial gives D(y) for the 16 columns; clears its 16
+//      targets of this row's z-buffers (double buffered across rows).
+//   -- barrier --
+//   B  the warp scatters its 512 sources (lane-interleaved) into the left and right
+//      z-buffers with atomicMin on a ((255 - depth) << 24 | RGB) entry.
+//   -- barrier --
+//   C  reads its 16 targets' entries, fills holes (warp scans for the nearest filled
+//      target on each side), formats and stores the outputs.
 #include "dibr.h"
 #include "dibr_internal.h"
 #include "dibr_ptx.cuh"
@@ -20,96 +33,142 @@
 namespace dibr {
 namespace {
 
+constexpr int kNoTarget = 0x7FFFFFFF;
+
 __device__ __forceinline__ uint32_t bsel(const uint32_t *w, int j) {
   return (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
 }
 
-__device__ __forceinline__ void lds48(const uint8_t *s, uint32_t (&w)[12]) {
-  const uint4 *p = reinterpret_cast<const uint4 *>(s);
-  const uint4 a = p[0], b = p[1], c = p[2];
-  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-  w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
-}
-
-// BT.601 luminance in exact thousandths, rounded half up (the depth-map reading).
+// BT.601 luminance in exact thousandths, rounded half up (the depth-map reading):
+// (299 R + 587 G + 114 B + 500) / 1000, the division as a multiply-high by
+// ceil(2^32 / 1000), exact for numerators below 6.1e6.
 __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b) {
-  return (299u * r + 587u * g + 114u * b + 500u) / 1000u;
+  return __umulhi(299u * r + 587u * g + 114u * b + 500u, 4294968u);
 }
 
-__device__ __forceinline__ uint4 luma_chunk(const uint32_t (&w)[12]) {
-  uint32_t y[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int i = 0; i < 16; ++i)
-    y[i >> 2] |= luma8(bsel(w, 3 * i), bsel(w, 3 * i + 1), bsel(w, 3 * i + 2)) << (8 * (i & 3));
-  return make_uint4(y[0], y[1], y[2], y[3]);
+// The same luminance of the pixel held in bytes 0..2 (S = 0) or 1..3 (S = 8) of w, as
+// three byte dot products: 299 = 255 + 44, 587 = 255 + 255 + 77, 114.
+template <int S>
+__device__ __forceinline__ uint32_t luma_dp(uint32_t w) {
+  uint32_t n = __dp4a(w, 0x0072FFFFu << S, 500u);
+  n = __dp4a(w, 0x0000FF2Cu << S, n);
+  n = __dp4a(w, 0x00004D00u << S, n);
+  return __umulhi(n, 4294968u);
 }
 
-// 5x5 binomial smoothing of the luminance for the 16 pixels of one chunk:
-// D = (sum_ij b_i b_j Y[clamp(y+i)][clamp(x+j)] + 128) >> 8, b = (1 4 6 4 1).
-__device__ __forceinline__ uint4 binom5_chunk(const uint8_t *yring, int ystride, int y, int H,
-                                              int W, int x0) {
-  const uint8_t *rows[5];
+// Luminance of one packed pixel word (R, G, B in the low three bytes).
+__device__ __forceinline__ uint32_t luma_px(uint32_t c) { return luma_dp<0>(c); }
+
+// Luminance of columns x0-2 .. x0+17 (clamped to [0, W-1]) of one input row held in
+// shared memory, as 10 words of two 16-bit lanes: yp[2q] = columns (4q, 4q+2) and
+// yp[2q+1] = (4q+1, 4q+3) of the window, the layout the vertical cascade works on.
+__device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32_t (&yp)[10]) {
+  uint32_t y[20];
+  if (x0 >= 16 && x0 + 18 <= W) {
+    // bytes 3*x0-8 .. 3*x0+55 (8-byte and 16-byte aligned loads); column j at byte 2+3j
+    uint32_t b[16];
+    const uint2 l = *reinterpret_cast<const uint2 *>(row + 3 * x0 - 8);
+    const uint4 m0 = *reinterpret_cast<const uint4 *>(row + 3 * x0);
+    const uint4 m1 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 16);
+    const uint4 m2 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 32);
+    const uint2 r = *reinterpret_cast<const uint2 *>(row + 3 * x0 + 48);
+    b[0] = l.x; b[1] = l.y;
+    b[2] = m0.x; b[3] = m0.y; b[4] = m0.z; b[5] = m0.w;
+    b[6] = m1.x; b[7] = m1.y; b[8] = m1.z; b[9] = m1.w;
+    b[10] = m2.x; b[11] = m2.y; b[12] = m2.z; b[13] = m2.w;
+    b[14] = r.x; b[15] = r.y;
 #pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int r = min(max(y + i - 2, 0), H - 1);
-    rows[i] = yring + (r % kYRing) * ystride;
-  }
-  const uint32_t kb[5] = {1u, 4u, 6u, 4u, 1u};
-  uint32_t V[20];
-#pragma unroll
-  for (int j = 0; j < 20; ++j) V[j] = 0u;
-  if (x0 >= 4 && x0 + 18 <= W) {
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const uint8_t *p = rows[i] + x0;
-      const uint32_t l = *reinterpret_cast<const uint32_t *>(p - 4);
-      const uint4 m = *reinterpret_cast<const uint4 *>(p);
-      const uint32_t r = *reinterpret_cast<const uint32_t *>(p + 16);
-      const uint32_t w[6] = {l, m.x, m.y, m.z, m.w, r};
-#pragma unroll
-      for (int j = 0; j < 20; ++j) V[j] += kb[i] * bsel(w, j + 2);
+    for (int j = 0; j < 20; ++j) {
+      const int o = 2 + 3 * j, q = o >> 2;
+      if ((o & 3) == 0) y[j] = luma_dp<0>(b[q]);
+      else if ((o & 3) == 1) y[j] = luma_dp<8>(b[q]);
+      else y[j] = luma_dp<0>(__funnelshift_r(b[q], b[q + 1], 8 * (o & 3)));
     }
   } else {
 #pragma unroll
     for (int j = 0; j < 20; ++j) {
       const int xc = min(max(x0 - 2 + j, 0), W - 1);
-#pragma unroll
-      for (int i = 0; i < 5; ++i) V[j] += kb[i] * rows[i][xc];
+      const uint8_t *p = row + 3 * xc;
+      y[j] = luma8(p[0], p[1], p[2]);
     }
   }
-  uint32_t d[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const uint32_t s = V[i] + 4u * V[i + 1] + 6u * V[i + 2] + 4u * V[i + 3] + V[i + 4];
-    d[i >> 2] |= ((s + 128u) >> 8) << (8 * (i & 3));
+  for (int q = 0; q < 5; ++q) {
+    yp[2 * q] = y[4 * q] | (y[4 * q + 2] << 16);
+    yp[2 * q + 1] = y[4 * q + 1] | (y[4 * q + 3] << 16);
+  }
+}
+
+// Vertical binomial [1 4 6 4 1] as four cascaded [1 1] sums over the stream of
+// luminance rows.  The 20 columns are held as 10 words of two 16-bit lanes: lo[q] =
+// columns (4q, 4q+2), hi[q] = (4q+1, 4q+3) of the window x0-2 .. x0+17.  After a row n
+// is fed, p0 = Y(n), p1 = Y(n-1)+Y(n), p2 and p3 the next sums; feeding row n+1 returns
+// sum_i C(4,i) Y(n-3+i), the vertical binomial centred on row n-1.  All sums stay below
+// 16 * 255, so the lanes never carry into each other.
+struct VCascade {
+  uint32_t p0[10], p1[10], p2[10], p3[10];
+
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) p0[i] = p1[i] = p2[i] = p3[i] = 0u;
+  }
+  // feeds one row (16-bit lane pairs); V receives the vertical sums (valid from the
+  // fifth row on)
+  __device__ __forceinline__ void feed(const uint32_t (&y)[10], uint32_t (&V)[10]) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const uint32_t a1 = p0[i] + y[i];
+      const uint32_t a2 = p1[i] + a1;
+      const uint32_t a3 = p2[i] + a2;
+      V[i] = p3[i] + a3;
+      p0[i] = y[i];
+      p1[i] = a1;
+      p2[i] = a2;
+      p3[i] = a3;
+    }
+  }
+  // feeds the newest row again (the image's last row repeated below the image)
+  __device__ __forceinline__ void feed_repeat(uint32_t (&V)[10]) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const uint32_t a1 = p0[i] + p0[i];
+      const uint32_t a2 = p1[i] + a1;
+      const uint32_t a3 = p2[i] + a2;
+      V[i] = p3[i] + a3;
+      p1[i] = a1;
+      p2[i] = a2;
+      p3[i] = a3;
+    }
+  }
+};
+
+// Horizontal binomial of the vertical sums and rounding: D = (sum + 128) >> 8 for the 16
+// own columns (window columns 2..17), packed 4 per word.
+__device__ __forceinline__ uint4 binom_h(const uint32_t (&V)[10]) {
+  uint32_t d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t E0 = V[2 * k], O0 = V[2 * k + 1], E1 = V[2 * k + 2], O1 = V[2 * k + 3];
+    const uint32_t se = __byte_perm(E0, E1, 0x5432);  // (V[4k+2], V[4k+4])
+    const uint32_t so = __byte_perm(O0, O1, 0x5432);  // (V[4k+3], V[4k+5])
+    const uint32_t pe = E0 + E1 + 4u * (O0 + so) + 6u * se;  // columns 4k, 4k+2
+    const uint32_t po = O0 + O1 + 4u * (se + E1) + 6u * so;  // columns 4k+1, 4k+3
+    const uint32_t de = ((pe + 0x00800080u) >> 8) & 0x00FF00FFu;
+    const uint32_t dd = ((po + 0x00800080u) >> 8) & 0x00FF00FFu;
+    d[k] = de | (dd << 8);
   }
   return make_uint4(d[0], d[1], d[2], d[3]);
 }
 
-// z-buffer key: (depth + 1) in the high half (0 = empty target), source column in the
-// low half, reversed in the left view so that atomicMax prefers the smaller column.
-__device__ __forceinline__ int key_src(uint32_t k, bool left) {
-  const uint32_t lo = k & 0xFFFFu;
-  return left ? static_cast<int>(0xFFFFu - lo) : static_cast<int>(lo);
-}
-
-// Row-local hole fill: nearest filled target on each side; the one with the smaller
-// depth (background) wins, the left one on a tie; a single side wins alone; with none,
-// the target keeps its own input column.
-__device__ __noinline__ int fill_src(const uint32_t *zb, int t, int W, bool left) {
-  int l = t - 1;
-  while (l >= 0 && zb[l] == 0u) --l;
-  int r = t + 1;
-  while (r < W && zb[r] == 0u) ++r;
-  const uint32_t kl = l >= 0 ? zb[l] : 0u, kr = r < W ? zb[r] : 0u;
-  uint32_t k;
-  if (kl && kr) k = (kl >> 16) <= (kr >> 16) ? kl : kr;
-  else if (kl) k = kl;
-  else if (kr) k = kr;
-  else return t;
-  return key_src(k, left);
-}
+// z-buffer entry: ((255 - depth) << 24) | RGB of the source, reduced with atomicMin
+// into a buffer initialised to kEmpty.  The smallest entry has the largest depth
+// (nearest source).  Two sources with equal depth have equal shifts and so never meet
+// on one target, so the colour bits never decide a collision; the winner's colour is
+// read straight from its entry.  kEmpty cannot be a real entry: it would need depth 0
+// for a white pixel, and every depth rule gives a white pixel a depth of at least 1
+// (binomial: its own weight 36/256; luminance: 255; cross-bilateral: its own weight 1
+// among at most 289).
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // Packed RGB (3 bytes) of column x of a row held in shared memory.
 __device__ __forceinline__ uint32_t rgb_at(const uint8_t *row, int x) {
@@ -118,12 +177,113 @@ __device__ __forceinline__ uint32_t rgb_at(const uint8_t *row, int x) {
   return __funnelshift_r(wp[0], wp[1], (off & 3u) * 8u) & 0xFFFFFFu;
 }
 
-// Places the 3 bytes of c at pixel i of a packed RGB word array.
-template <int N>
-__device__ __forceinline__ void put3(uint32_t (&w)[N], int i, uint32_t c) {
-  const int o = 3 * i, j = o >> 2, s = (o & 3) * 8;
-  w[j] |= c << s;
-  if (s > 8) w[j + 1] |= c >> (32 - s);
+// Sixteen 3-byte colours (low bytes of c[i]) packed into 12 words.
+__device__ __forceinline__ void pack16(const uint32_t (&c)[16], uint32_t (&w)[12]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[3 * k] = __byte_perm(c[4 * k], c[4 * k + 1], 0x4210);
+    w[3 * k + 1] = __byte_perm(c[4 * k + 1], c[4 * k + 2], 0x5421);
+    w[3 * k + 2] = __byte_perm(c[4 * k + 2], c[4 * k + 3], 0x6542);
+  }
+}
+
+// Nearest filled target at or below t (or -1) / at or above t (or kNoTarget), searched
+// by the whole warp 32 targets at a time (all lanes call it together): the path for
+// holes whose neighbours lie outside the warp's own targets.
+__device__ __noinline__ int warp_walk_left(const uint32_t *zb, int t, int lane) {
+  for (int base = t; base >= 0; base -= 32) {
+    const int i = base - lane;
+    const uint32_t b = __ballot_sync(0xffffffffu, i >= 0 && zb[i] != kEmpty);
+    if (b) return base - (__ffs(b) - 1);
+  }
+  return -1;
+}
+
+__device__ __noinline__ int warp_walk_right(const uint32_t *zb, int t, int W, int lane) {
+  for (int base = t; base < W; base += 32) {
+    const int i = base + lane;
+    const uint32_t b = __ballot_sync(0xffffffffu, i < W && zb[i] != kEmpty);
+    if (b) return base + (__ffs(b) - 1);
+  }
+  return kNoTarget;
+}
+
+// Entries shown by the 16 targets of this thread in one view: the z-buffer winner, or
+// for a hole the winner of the nearest filled target on the background (smaller
+// depth) side -- the left one on a tie -- or of the only side; with no filled target in
+// the row, the input pixel at the hole itself (row-local inpainting).
+//
+// Neighbours outside the thread's 16 targets come from the nearest lower / higher lane
+// that has a filled target (ballot + shuffle) or, past the warp's 512 targets, from a
+// warp-wide search of the z-buffer.
+__device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0,
+                                             int npx, int W, int lane, int warp_lo, int warp_hi,
+                                             uint32_t (&k)[16]) {
+  const uint32_t zs = smem_addr(zb);
+  if (npx > 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 u = lds_u32x4(zs + 4u * (x0 + 4 * q));
+      k[4 * q] = u.x; k[4 * q + 1] = u.y; k[4 * q + 2] = u.z; k[4 * q + 3] = u.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) k[i] = 0u;
+  }
+  const uint32_t rowmask = npx >= 16 ? 0xFFFFu : ((1u << max(npx, 0)) - 1u);
+  uint32_t m = 0u;
+#pragma unroll
+  for (int i = 0; i < 16; ++i)
+    if (k[i] != kEmpty) m |= 1u << i;
+  m &= rowmask;
+  const uint32_t holes = ~m & rowmask;
+  if (!__any_sync(0xffffffffu, holes != 0u)) return;
+
+  // filled targets nearest to this lane's chunk on either side
+  const int last = m ? x0 + 31 - __clz(m) : -1;
+  const int first = m ? x0 + __ffs(m) - 1 : kNoTarget;
+  const uint32_t lanes = __ballot_sync(0xffffffffu, m != 0u);
+  const uint32_t lower = lanes & ((1u << lane) - 1u);
+  const uint32_t upper = lanes & ~((2u << lane) - 1u);
+  int prev = __shfl_sync(0xffffffffu, last, lower ? 31 - __clz(lower) : lane);
+  int next = __shfl_sync(0xffffffffu, first, upper ? __ffs(upper) - 1 : lane);
+  if (!lower) prev = -1;
+  if (!upper) next = kNoTarget;
+  if (__any_sync(0xffffffffu, holes && prev < 0)) {
+    const int wl = warp_lo > 0 ? warp_walk_left(zb, warp_lo - 1, lane) : -1;
+    if (prev < 0) prev = wl;
+  }
+  if (__any_sync(0xffffffffu, holes && next == kNoTarget)) {
+    const int wr = warp_hi < W ? warp_walk_right(zb, warp_hi, W, lane) : kNoTarget;
+    if (next == kNoTarget) next = wr;
+  }
+  // one pass per run of holes: its two neighbours and the farther of them fill it
+  uint32_t rest = holes;
+  while (rest) {
+    const int i0 = __ffs(rest) - 1;
+    const int len = __ffs(~(rest >> i0)) - 1;
+    const uint32_t run = ((1u << len) - 1u) << i0;
+    const uint32_t below = m & ((1u << i0) - 1u);
+    const uint32_t above = m & ~((1u << (i0 + len)) - 1u);
+    const int l = below ? x0 + 31 - __clz(below) : prev;
+    const int r = above ? x0 + __ffs(above) - 1 : next;
+    const uint32_t kl = l >= 0 ? lds_u32(zs + 4u * l) : kEmpty;
+    const uint32_t kr = r < W ? lds_u32(zs + 4u * r) : kEmpty;
+    uint32_t s = kEmpty;
+    if (kl != kEmpty && kr != kEmpty) s = (kl >> 24) >= (kr >> 24) ? kl : kr;  // smaller depth
+    else if (kl != kEmpty) s = kl;
+    else if (kr != kEmpty) s = kr;
+    if (s != kEmpty) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if ((run >> j) & 1u) k[j] = s;
+    } else {  // no filled target anywhere in the row: the input pixel stays
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if ((run >> j) & 1u) k[j] = rgb_at(rgbrow, x0 + j);
+    }
+    rest &= ~run;
+  }
 }
 
 // Rounded-up per-byte mean of two packed colours: (a + b + 1) >> 1 in every byte.
@@ -169,104 +329,99 @@ __device__ __forceinline__ void store16(uint8_t *p, uint4 v, int npx) {
   }
 }
 
-__global__ void __launch_bounds__(kMaxConsumers + 32, 1)
+template <int kMaxThreads, int kMinBlocks>
+__global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     band_kernel(const __grid_constant__ BandArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  const BandSmem L = band_smem_layout(a.nb, a.srow, a.ystride, a.nch, a.depth_src);
+  const BandSmem L = band_smem_layout(a.nb, a.srow, a.nch, a.depth_src);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar);
-  uint64_t *empty = full + kMaxRing;
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L.flags);
-  int32_t *lut_h = reinterpret_cast<int32_t *>(smem + L.lut);
-  int32_t *lut_n = reinterpret_cast<int32_t *>(smem + L.zb);  // gather mode only
+  int4 *lut4 = reinterpret_cast<int4 *>(smem + L.lut);  // {-hL, -hR, (255 - d) << 24, 0}
   uint8_t *ring = smem + L.ring;
-  uint8_t *yring = smem + L.yring;
   uint8_t *drow = smem + L.drow;
-  uint32_t *zbL = reinterpret_cast<uint32_t *>(smem + L.zb);
-  uint32_t *zbR = zbL + a.nch * kChunk;
+  uint32_t *zb0 = reinterpret_cast<uint32_t *>(smem + L.zb);  // [2 rows][L, R][nch*16]
+  int32_t *lut_n = reinterpret_cast<int32_t *>(smem + L.zb);  // literal gather only
 
   const int tid = threadIdx.x, nc = a.nc, W = a.W, H = a.H, nb = a.nb;
+  const int zlen = a.nch * kChunk;
   const int ys = static_cast<int>(static_cast<int64_t>(blockIdx.x) * H / a.grid);
   const int ye = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * H / a.grid);
   const bool binom = a.depth_src == DS_BINOM5;
+  const bool forward = a.warp_mode == DIBR_WARP_FORWARD;
   const int halo = binom ? 2 : 0;
   const int la = max(ys - halo, 0), lb = min(ye + halo, H);
+  const int nload = lb - la;
 
-  const bool forward = a.warp_mode == DIBR_WARP_FORWARD;
   for (int i = tid; i < 256; i += blockDim.x) {
-    lut_h[i] = a.lut_h[i];
+    lut4[i] = make_int4(-static_cast<int16_t>(a.lut_h[i] & 0xFFFF), -(a.lut_h[i] >> 16),
+                        static_cast<int>((255u - static_cast<uint32_t>(i)) << 24), 0);
     if (!forward) lut_n[i] = a.lut_n[i];
   }
   if (tid == 0) {
-    for (int i = 0; i < nb; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    *abort_flag = 0;
+    for (int i = 0; i < nb; ++i) mbar_init(&full[i], 1);
     fence_mbar_init();
   }
   __syncthreads();
   if (ys >= ye) return;
 
-  // ------------------------------------------------------------------ producer warp
-  if (tid >= nc) {
-    const int lane = tid - nc;
-    if (lane == 0) prefetch_tensormap(&a.tmap);
-    int issued = 0;
-    bool ok = true;
-    for (int k = 0; k < lb - la; ++k) {
-      const int s = k % nb;
-      if (k >= nb) {
-        int got = 1;
-        if (lane == 0) {
-          const unsigned long long t0 = global_ns();
-          while (!mbar_try_wait(&empty[s], ((k / nb) - 1) & 1)) {
-            if (*abort_flag || global_ns() - t0 > a.timeout_ns) {
-              got = 0;
-              break;
-            }
+  // Row k = r - la of the CTA's rows goes to slot k % nb.  Warp 0 issues the loads of
+  // rows [issued, upto); the caller guarantees every earlier occupant of those slots
+  // has been released by all threads (a barrier separates the last use from the call).
+  int issued = 0;
+  auto issue_loads = [&](int upto) {
+    upto = min(upto, nload);
+    if (tid < 32) {
+      if (tid == 0 && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(&a.tmap);
+      for (int k = issued; k < upto; ++k) {
+        const int s = k % nb;
+        uint8_t *dst = ring + s * a.srow;
+        if (a.load_mode == LM_BULK) {
+          if (tid == 0) {
+            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(a.row_bytes));
+            bulk_load(dst, a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes),
+                      &full[s]);
+          }
+        } else {
+          if (tid == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
+          __syncwarp();
+          for (int i = tid; i < a.nbox; i += 32) {
+            if (a.load_mode == LM_T3)
+              tma_load_3d(dst + i * a.box_bytes, &a.tmap, 0, i * a.box_step, la + k, &full[s]);
+            else
+              tma_load_2d(dst + i * a.box_bytes, &a.tmap, i * a.box_step, la + k, &full[s]);
           }
         }
-        got = __shfl_sync(0xffffffffu, got, 0);
-        if (!got) {
-          ok = false;
-          break;
-        }
       }
-      if (lane == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(a.nbox * kBoxBytes));
-      __syncwarp();
-      uint8_t *dst = ring + s * a.srow;
-      for (int i = lane; i < a.nbox; i += 32)
-        tma_load_2d(dst + i * kBoxBytes, &a.tmap, i * kBoxBytes, la + k, &full[s]);
-      issued = k + 1;
     }
-    if (!ok && lane == 0) {
-      if (!*abort_flag) atomicOr(a.status, ST_TIMEOUT_EMPTY);
-      // let every copy already issued land before the CTA's shared memory goes away
-      for (int k = max(0, issued - nb); k < issued; ++k)
-        if (!mbar_wait_bounded(&full[k % nb], (k / nb) & 1, a.timeout_ns))
-          atomicOr(a.status, ST_TIMEOUT_DRAIN);
+    issued = max(issued, upto);
+  };
+  issue_loads(nb);
+  // the CTA's rows beyond the ring's first fill go to L2 now, so that every later ring
+  // refill is an L2 hit: the whole input streams from HBM at the start of the launch
+  if (a.l2_prefetch && tid < 32) {
+    if (a.load_mode == LM_BULK) {
+      for (int k = nb + tid; k < nload; k += 32)
+        bulk_prefetch_l2(a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes));
+    } else {
+      for (int j = tid; j < (nload - nb) * a.nbox; j += 32) {
+        const int k = nb + j / a.nbox, i = j % a.nbox;
+        if (a.load_mode == LM_T3) tma_prefetch_3d(&a.tmap, 0, i * a.box_step, la + k);
+        else tma_prefetch_2d(&a.tmap, i * a.box_step, la + k);
+      }
     }
-    return;
   }
 
   // ---------------------------------------------------------------------- consumers
+  const int lane = tid & 31;
+  const int x0 = tid * kChunk;
+  const int npx = max(0, min(kChunk, W - x0));
+  const bool active = npx > 0;
+  const int warp_lo = (tid & ~31) * kChunk;
+  const int warp_hi = min(W, warp_lo + 32 * kChunk);
   bool timed_out = false;
   auto slot = [&](int r) { return ring + ((r - la) % nb) * a.srow; };
   auto wait_row = [&](int r) {
     const int k = r - la;
     if (!mbar_wait_bounded(&full[k % nb], (k / nb) & 1, a.timeout_ns)) timed_out = true;
-  };
-  auto release_row = [&](int r) {
-    if (tid == 0) mbar_arrive(&empty[(r - la) % nb]);
-  };
-  auto luma_row = [&](int r) {
-    const uint8_t *src = slot(r);
-    uint8_t *yd = yring + (r % kYRing) * a.ystride;
-    for (int c = tid; c < a.nch; c += nc) {
-      uint32_t w[12];
-      lds48(src + 48 * c, w);
-      *reinterpret_cast<uint4 *>(yd + 16 * c) = luma_chunk(w);
-    }
   };
 
   const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
@@ -276,62 +431,74 @@ __global__ void __launch_bounds__(kMaxConsumers + 32, 1)
   const bool want_hsbs = (a.outputs & DIBR_OUT_HSBS) != 0;
   bool aborted = false;
 
+  VCascade vc;
+  vc.clear();
   if (binom) {
-    // luminance of the rows above the band and of the first rows of the band
-    const int pend = min(ys + 2, lb - 1);
-    for (int r = la; r <= pend; ++r) {
-      wait_row(r);
-      luma_row(r);
+    // rows clamp(ys-2) .. clamp(ys+1) into the cascade
+    const int pend = min(ys + 1, lb - 1);
+    for (int r = la; r <= pend; ++r) wait_row(r);
+#pragma unroll 1
+    for (int i = -2; i <= 1; ++i) {
+      const int r = min(max(ys + i, 0), H - 1);
+      uint32_t yq[10] = {0u}, V[10];
+      if (active) luma20(slot(r), x0, W, yq);
+      vc.feed(yq, V);
     }
     if (consumer_sync_or(timed_out, nc)) aborted = true;
-    else
-      for (int r = la; r <= pend; ++r)
-        if (r < ys || r >= ye) release_row(r);
+    else issue_loads((ys - la) + nb);  // the rows above the band are done with
   }
 
   for (int y = ys; y < ye && !aborted; ++y) {
-    // ---- phase A: depth of row y (and luminance of row y+3), clear the z-buffers
+    uint32_t *zl = zb0 + (y & 1) * 2 * zlen;
+    uint32_t *zr = zl + zlen;
+    // ---- phase A: depth of row y in registers; clear this row's z-buffer targets
+    uint4 d = make_uint4(0u, 0u, 0u, 0u);
     if (binom) {
-      const int r3 = y + 3;
-      if (r3 < lb) {
-        wait_row(r3);
-        luma_row(r3);
+      const int r2 = y + 2;
+      if (r2 < lb) wait_row(r2);
+      uint32_t V[10];
+      if (r2 < H) {
+        uint32_t yq[10] = {0u};
+        if (active) luma20(slot(r2), x0, W, yq);
+        vc.feed(yq, V);
+      } else {
+        vc.feed_repeat(V);  // rows below the image repeat row H-1
       }
+      d = binom_h(V);
     } else {
       wait_row(y);
-    }
-    for (int c = tid; c < a.nch; c += nc) {
-      const int x0 = c * kChunk;
-      uint4 d;
-      if (binom) {
-        d = binom5_chunk(yring, a.ystride, y, H, W, x0);
-      } else if (a.depth_src == DS_LUMA) {
-        uint32_t w[12];
-        lds48(slot(y) + 48 * c, w);
-        d = luma_chunk(w);
-      } else {
-        const uint8_t *dp = a.depth_in + static_cast<int64_t>(y) * a.depth_in_pitch + x0;
-        const int npx = min(kChunk, W - x0);
-        if (npx == kChunk && (reinterpret_cast<uintptr_t>(dp) & 15u) == 0) {
-          d = *reinterpret_cast<const uint4 *>(dp);
-        } else {
+      if (active) {
+        if (a.depth_src == DS_LUMA) {
+          const uint8_t *row = slot(y);
           uint32_t w[4] = {0u, 0u, 0u, 0u};
-          for (int i = 0; i < npx; ++i) w[i >> 2] |= static_cast<uint32_t>(dp[i]) << (8 * (i & 3));
+#pragma unroll
+          for (int j = 0; j < 16; ++j) w[j >> 2] |= luma_px(rgb_at(row, min(x0 + j, W - 1))) << (8 * (j & 3));
           d = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+          const uint8_t *dp = a.depth_in + static_cast<int64_t>(y) * a.depth_in_pitch + x0;
+          if (npx == kChunk && (reinterpret_cast<uintptr_t>(dp) & 15u) == 0) {
+            d = *reinterpret_cast<const uint4 *>(dp);
+          } else {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (int i = 0; i < npx; ++i) w[i >> 2] |= static_cast<uint32_t>(dp[i]) << (8 * (i & 3));
+            d = make_uint4(w[0], w[1], w[2], w[3]);
+          }
         }
       }
-      *reinterpret_cast<uint4 *>(drow + x0) = d;
-      if (want_depth)
-        store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d,
-                min(kChunk, W - x0));
-      if (forward) {
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        uint4 *zl = reinterpret_cast<uint4 *>(zbL + x0);
-        uint4 *zr = reinterpret_cast<uint4 *>(zbR + x0);
+    }
+    if (active && want_depth)
+      store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d, npx);
+    if (forward) {
+      if (active) *reinterpret_cast<uint4 *>(drow + x0) = d;
+      // clear this warp's 512 targets of both views, consecutive lanes on consecutive
+      // 16-byte words (no bank conflicts)
+      const uint4 e = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          zl[q] = z;
-          zr[q] = z;
+      for (int q = 0; q < 4; ++q) {
+        const int t = warp_lo + 4 * (32 * q + lane);
+        if (t < zlen) {
+          *reinterpret_cast<uint4 *>(zl + t) = e;
+          *reinterpret_cast<uint4 *>(zr + t) = e;
         }
       }
     }
@@ -339,133 +506,127 @@ __global__ void __launch_bounds__(kMaxConsumers + 32, 1)
       aborted = true;
       break;
     }
+    // every thread is past phase C of row y-1: the slots of rows < y can be refilled
+    issue_loads((y - la) + nb);
 
-    // ---- phase B: forward warp, occlusion by atomicMax on (depth, column) keys
+    // ---- phase B: forward warp; occlusion by atomicMin on (255 - depth, RGB) entries
+    const uint8_t *rgbrow = slot(y);
+    const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
     if (forward) {
-      for (int c = tid; c < a.nch; c += nc) {
-        const int x0 = c * kChunk;
-        const uint4 dq = *reinterpret_cast<const uint4 *>(drow + x0);
-        const uint32_t dw[4] = {dq.x, dq.y, dq.z, dq.w};
-#pragma unroll
-        for (int i = 0; i < kChunk; ++i) {
-          const int x = x0 + i;
-          if (x < W) {
-            const uint32_t d = bsel(dw, i);
-            const int32_t lh = lut_h[d];
-            const int hl = static_cast<int16_t>(lh & 0xFFFF), hr = lh >> 16;
-            const int tl = x - hl, tr = x - hr;
-            if (static_cast<unsigned>(tl) < static_cast<unsigned>(W))
-              atomicMax(&zbL[tl], ((d + 1u) << 16) | (0xFFFFu - static_cast<uint32_t>(x)));
-            if (static_cast<unsigned>(tr) < static_cast<unsigned>(W))
-              atomicMax(&zbR[tr], ((d + 1u) << 16) | static_cast<uint32_t>(x));
-          }
+      // the warp's 512 sources, consecutive lanes on consecutive columns, so that the
+      // atomics of one instruction land on distinct banks (shifts vary slowly)
+      const int xb = warp_lo + lane;
+      const uint32_t ob = 3u * static_cast<uint32_t>(xb);
+      const uint32_t cws = smem_addr(rgbrow) + (ob & ~3u);  // the lane's colours: +96 bytes per step
+      const uint32_t sh = (ob & 3u) * 8u;
+      const uint32_t ds = smem_addr(drow) + static_cast<uint32_t>(xb);
+      const uint32_t ls = smem_addr(lut4);
+      const uint32_t zls = smem_addr(zl), zrs = smem_addr(zr);
+      const bool full_warp = warp_hi - warp_lo == 32 * kChunk;
+#pragma unroll 4
+      for (int i = 0; i < kChunk; ++i) {
+        const int x = xb + 32 * i;
+        if (full_warp || x < warp_hi) {
+          const uint32_t dv = lds_u8(ds + 32 * i);
+          const int4 lh = lds_s32x4(ls + 16 * dv);
+          const uint32_t w0 = lds_u32(cws + 96 * i), w1 = lds_u32(cws + 96 * i + 4);
+          const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh.z);
+          const int tl = x + lh.x, tr = x + lh.y;
+          if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
+          if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
         }
       }
     }
     consumer_sync(nc);
 
     // ---- phase C: resolve winners, fill holes, compose and store the outputs
-    const uint8_t *rgbrow = slot(y);
-    for (int c = tid; c < a.nch; c += nc) {
-      const int x0 = c * kChunk;
-      const int npx = min(kChunk, W - x0);
-      uint32_t cl[16], cr[16];
-      if (forward) {
-        const uint4 *zl = reinterpret_cast<const uint4 *>(zbL + x0);
-        const uint4 *zr = reinterpret_cast<const uint4 *>(zbR + x0);
-        uint32_t kL[16], kR[16];
+    uint32_t kl[16], kr[16];
+    if (forward) {
+      resolve_view(zl, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kl);
+      resolve_view(zr, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kr);
+    } else {
+      // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint4 u = zl[q], v = zr[q];
-          kL[4 * q] = u.x; kL[4 * q + 1] = u.y; kL[4 * q + 2] = u.z; kL[4 * q + 3] = u.w;
-          kR[4 * q] = v.x; kR[4 * q + 1] = v.y; kR[4 * q + 2] = v.z; kR[4 * q + 3] = v.w;
-        }
-#pragma unroll
-        for (int i = 0; i < kChunk; ++i) {
-          if (i < npx) {
-            const int sl = kL[i] ? key_src(kL[i], true) : fill_src(zbL, x0 + i, W, true);
-            const int sr = kR[i] ? key_src(kR[i], false) : fill_src(zbR, x0 + i, W, false);
-            cl[i] = rgb_at(rgbrow, sl);
-            cr[i] = rgb_at(rgbrow, sr);
-          } else {
-            cl[i] = 0u;
-            cr[i] = 0u;
-          }
-        }
-      } else {
-        // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
-        const uint4 dq = *reinterpret_cast<const uint4 *>(drow + x0);
-        const uint32_t dw[4] = {dq.x, dq.y, dq.z, dq.w};
-#pragma unroll
-        for (int i = 0; i < kChunk; ++i) {
-          if (i < npx) {
-            const int x = x0 + i;
-            const int n = lut_n[bsel(dw, i)];
-            int sl = (510 * x + n) / 510, sr = (510 * x - n) / 510;
-            if (static_cast<unsigned>(sl) >= static_cast<unsigned>(W)) sl = x;
-            if (static_cast<unsigned>(sr) >= static_cast<unsigned>(W)) sr = x;
-            cl[i] = rgb_at(rgbrow, sl);
-            cr[i] = rgb_at(rgbrow, sr);
-          } else {
-            cl[i] = 0u;
-            cr[i] = 0u;
-          }
-        }
+      for (int i = 0; i < kChunk; ++i) {
+        const int x = min(x0 + i, W - 1);
+        const int n = lut_n[bsel(dw, i)];
+        int sl = (510 * x + n) / 510, sr = (510 * x - n) / 510;
+        if (static_cast<unsigned>(sl) >= static_cast<unsigned>(W)) sl = x;
+        if (static_cast<unsigned>(sr) >= static_cast<unsigned>(W)) sr = x;
+        kl[i] = active ? rgb_at(rgbrow, sl) : 0u;
+        kr[i] = active ? rgb_at(rgbrow, sr) : 0u;
       }
+    }
+    if (active) {
       const int64_t ro = static_cast<int64_t>(y) * a.out_pitch;
+      uint32_t w[12];
       if (want_l) {
-        uint32_t w[12] = {0u};
-#pragma unroll
-        for (int i = 0; i < 16; ++i) put3(w, i, cl[i]);
+        pack16(kl, w);
         store48(a.out[O_LEFT] + ro + 3 * x0, w, npx);
       }
       if (want_r) {
-        uint32_t w[12] = {0u};
-#pragma unroll
-        for (int i = 0; i < 16; ++i) put3(w, i, cr[i]);
+        pack16(kr, w);
         store48(a.out[O_RIGHT] + ro + 3 * x0, w, npx);
       }
       if (want_ana) {
-        uint32_t w[12] = {0u};
+        uint32_t c[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) put3(w, i, (cl[i] & 0x0000FFu) | (cr[i] & 0xFFFF00u));
+        for (int i = 0; i < 16; ++i) c[i] = __byte_perm(kl[i], kr[i], 0x3650);  // R from L; G, B from R
+        pack16(c, w);
         store48(a.out[O_ANA] + ro + 3 * x0, w, npx);
       }
       if (want_hsbs) {
-        uint32_t wl[6] = {0u}, wr[6] = {0u};
+        uint32_t cl8[8], cr8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          put3(wl, j, avg_up(cl[2 * j], cl[2 * j + 1]) & 0xFFFFFFu);
-          put3(wr, j, avg_up(cr[2 * j], cr[2 * j + 1]) & 0xFFFFFFu);
+          cl8[j] = avg_up(kl[2 * j], kl[2 * j + 1]);
+          cr8[j] = avg_up(kr[2 * j], kr[2 * j + 1]);
+        }
+        uint32_t wl[6], wr[6];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          wl[3 * k] = __byte_perm(cl8[4 * k], cl8[4 * k + 1], 0x4210);
+          wl[3 * k + 1] = __byte_perm(cl8[4 * k + 1], cl8[4 * k + 2], 0x5421);
+          wl[3 * k + 2] = __byte_perm(cl8[4 * k + 2], cl8[4 * k + 3], 0x6542);
+          wr[3 * k] = __byte_perm(cr8[4 * k], cr8[4 * k + 1], 0x4210);
+          wr[3 * k + 1] = __byte_perm(cr8[4 * k + 1], cr8[4 * k + 2], 0x5421);
+          wr[3 * k + 2] = __byte_perm(cr8[4 * k + 2], cr8[4 * k + 3], 0x6542);
         }
         const int np = npx / 2;  // W is even, so chunks hold whole pairs
         store24(a.out[O_HSBS] + ro + 3 * (x0 / 2), wl, np);
         store24(a.out[O_HSBS] + ro + 3 * (W / 2 + x0 / 2), wr, np);
       }
     }
-    consumer_sync(nc);
-    release_row(y);
-    if (binom && y + 3 < lb && y + 3 >= ye) release_row(y + 3);
   }
 
   if (aborted && tid == 0) {
-    *abort_flag = 1;
     atomicOr(a.status, ST_TIMEOUT_FULL);
+    // let every copy already issued land before the CTA's shared memory goes away
+    for (int k = max(0, issued - nb); k < issued; ++k)
+      if (!mbar_wait_bounded(&full[k % nb], (k / nb) & 1, a.timeout_ns)) atomicOr(a.status, ST_TIMEOUT_DRAIN);
   }
 }
 
-}  // namespace
-
-cudaError_t launch_band(const BandArgs &a, int smem_bytes, cudaStream_t st) {
-  static bool attr_set = false;
+template <int T, int B>
+cudaError_t launch_variant(const BandArgs &a, int smem_bytes, cudaStream_t st) {
+  static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(band_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  band_kernel<<<a.grid, a.nc + 32, smem_bytes, st>>>(a);
+  band_kernel<T, B><<<a.grid, a.nc, smem_bytes, st>>>(a);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int band_max_threads(int ctas_per_sm) { return ctas_per_sm >= 2 ? 256 : kMaxConsumers; }
+
+cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
+  (void)ctas_per_sm;
+  return launch_variant<kMaxConsumers, 1>(a, smem_bytes, st);
 }
 
 }  // namespace dibr

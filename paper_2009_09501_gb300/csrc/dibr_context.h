@@ -38,8 +38,7 @@ struct dibr_ctx {
   int max_batch = 256;
   int *status_dev = nullptr;
   unsigned long long timeout_ns = 2000000000ull;  // 2 s per bounded device-side wait
-  int tune_ring = 0;         // 0: as many ring slots as shared memory allows
-  int tune_ctas_per_sm = 0;  // 0: as many as fit
+  dibr_tuning tuning{};      // zero fields: automatic
   uint64_t launches = 0;     // kernels launched by this context
 
   std::mutex err_mu;
@@ -60,7 +59,8 @@ struct dibr_ctx {
   void *dev_alloc(size_t bytes);
   void dev_free(void *p);
   dibr_status ensure(dibr::DevBuf &b, size_t bytes);
-  dibr_status plan_band(int W, int H, int depth_src, dibr::BandArgs &a, int &smem);
+  dibr_status plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, dibr::BandArgs &a,
+                        int &smem, int &per_sm);
   dibr_status encode_input(dibr::BandArgs &a, const uint8_t *dev_rgb, int64_t pitch);
   dibr_status enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
   dibr_status synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);

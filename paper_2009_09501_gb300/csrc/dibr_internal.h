@@ -11,8 +11,8 @@ namespace dibr {
 constexpr int kChunk = 16;          // pixels owned by one consumer thread per pass
 constexpr int kMaxRing = 8;         // TMA row-ring slots at most
 constexpr int kYRing = 6;           // luminance rows kept for the 5-row binomial
-constexpr int kBoxBytes = 256;      // TMA box width (bytes) for one input row segment
-constexpr int kMaxConsumers = 512;  // consumer threads per CTA at most
+constexpr int kBoxBytes = 256;      // 2-D TMA box width (bytes) for rows with 3*W not a multiple of 16
+constexpr int kMaxConsumers = 512;  // threads per CTA at most (8K rows use 480)
 constexpr int kMaxWidth = 7680;   // 8K UHD: the widest row whose z-buffers and ring fit on chip
 
 // How the depth of a row is obtained inside the band kernel.
@@ -20,6 +20,14 @@ enum DepthSource : int {
   DS_BINOM5 = 0,  // luminance + 5x5 binomial, computed on chip (rows +-2 of context)
   DS_LUMA = 1,    // luminance only
   DS_GLOBAL = 2   // read from a depth map in device memory (cross-bilateral pre-pass)
+};
+
+// How input rows reach shared memory.
+enum LoadMode : int {
+  LM_AUTO = 0,
+  LM_BULK = 1,   // one contiguous bulk copy (cp.async.bulk) per row
+  LM_T3 = 2,     // 3-D tensor {inner, 3W/inner, H}, boxes {inner, step, 1} (cp.async.bulk.tensor)
+  LM_T2 = 3      // 2-D tensor {3W, H}, boxes {256, 1}: any width
 };
 
 // Bits of the device status word.
@@ -31,17 +39,27 @@ enum { O_ANA = 0, O_LEFT = 1, O_RIGHT = 2, O_HSBS = 3, O_DEPTH = 4, O_COUNT = 5 
 // Per-image arguments of the band kernel.  The tensor map comes first for its 64-byte
 // alignment; the kernel receives the whole record as a __grid_constant__ parameter.
 struct BandArgs {
-  CUtensorMap tmap;  // input as a 2-D uint8 tensor {3W, H}, row stride = pitch
+  // input rows: a 3-D uint8 tensor {16, 3W/16, H} (strides 16, pitch) loaded in boxes of
+  // {16, box_step, 1} when 3W is a multiple of 16, else a 2-D tensor {3W, H} loaded in
+  // boxes of {256, 1}
+  CUtensorMap tmap;
+  const uint8_t *in;  // input base (bulk mode)
+  int64_t in_pitch;
   const uint8_t *depth_in;
   uint8_t *out[O_COUNT];
   int64_t out_pitch, depth_pitch, depth_in_pitch;
   int32_t W, H;
   int32_t nbox;      // TMA boxes per row
+  int32_t box_bytes; // bytes per box
+  int32_t box_step;  // box-to-box step of the tensor coordinate that walks along the row
+  int32_t tinner;    // LM_T3: bytes of a box's inner rows
+  int32_t load_mode; // LM_BULK, LM_T3 or LM_T2
+  int32_t row_bytes; // bytes of one input row (3W)
+  int32_t l2_prefetch; // prefetch the CTA's later rows into L2 at launch
   int32_t srow;      // bytes per ring slot
   int32_t nb;        // ring slots
-  int32_t ystride;   // bytes per luminance row (16-byte pads on both sides)
   int32_t nch;       // 16-pixel chunks per row
-  int32_t nc;        // consumer threads (multiple of 32); block = nc + 32
+  int32_t nc;        // threads per CTA, one 16-pixel chunk each (multiple of 32)
   int32_t grid;      // CTAs; CTA b owns rows [b*H/grid, (b+1)*H/grid)
   uint32_t outputs;  // DIBR_OUT_* bits
   int32_t warp_mode; // DIBR_WARP_*
@@ -54,29 +72,31 @@ struct BandArgs {
 
 // Shared-memory layout of the band kernel (bytes from the dynamic smem base).
 struct BandSmem {
-  int bar, flags, lut, ring, yring, drow, zb, total;
+  int bar, flags, lut, ring, drow, zb, total;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-__host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int ystride, int nch,
-                                                    int depth_src) {
+__host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, int depth_src) {
+  (void)depth_src;
   BandSmem s;
-  s.bar = 0;                       // full[kMaxRing], empty[kMaxRing] mbarriers
-  s.flags = 16 * kMaxRing;         // abort flag
-  s.lut = s.flags + 128;           // lut_h[256]
-  s.ring = round_up(s.lut + 1024, 256);
-  s.yring = s.ring + nb * srow;
-  int ybytes = depth_src == DS_BINOM5 ? kYRing * ystride : 0;
-  s.drow = round_up(s.yring + ybytes, 16);
-  // z-buffers of the forward warp; the literal gather keeps lut_n[256] here instead
+  s.bar = 0;                       // full[kMaxRing] mbarriers
+  s.flags = 8 * kMaxRing;          // reserved
+  s.lut = s.flags;                 // int4 lut[256]: {-hL[d], -hR[d], (255 - d) << 24, 0}
+  s.ring = round_up(s.lut + 4096, 128);
+  // depth of the current row, one byte per column (read back by the scatter)
+  s.drow = round_up(s.ring + nb * srow, 16);
+  // z-buffers of the forward warp, double buffered across rows: [2][L, R][nch * 16]
+  // (the literal gather keeps lut_n[256] here instead)
   s.zb = round_up(s.drow + nch * kChunk, 16);
-  s.total = s.zb + (2 * nch * kChunk * 4 > 1024 ? 2 * nch * kChunk * 4 : 1024);
+  const int zbytes = 4 * nch * kChunk * 4;
+  s.total = s.zb + (zbytes > 1024 ? zbytes : 1024);
   return s;
 }
 
 // Host launchers (dibr_band.cu, dibr_xbf.cu).
-cudaError_t launch_band(const BandArgs &a, int smem_bytes, cudaStream_t st);
+cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st);
+int band_max_threads(int ctas_per_sm);
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,
                        cudaStream_t st);

@@ -26,7 +26,8 @@ OUTPUT_BITS = {"anaglyph": 1, "left": 2, "right": 4, "hsbs": 8, "depth": 16}
 SYMBOLS = ("dibr_params_default", "dibr_validate", "dibr_shift_tables", "dibr_create",
            "dibr_destroy", "dibr_last_error", "dibr_stream", "dibr_synthesize_image",
            "dibr_enqueue_image", "dibr_synchronize", "dibr_synthesize_batch", "dibr_enqueue_batch",
-           "dibr_open_stream", "dibr_submit_frame", "dibr_poll", "dibr_close_stream")
+           "dibr_open_stream", "dibr_submit_frame", "dibr_poll", "dibr_close_stream",
+           "dibr_set_tuning", "dibr_get_tuning")
 
 
 class dibr_params(C.Structure):
@@ -55,6 +56,11 @@ class dibr_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("mem_budget_bytes", C.c_uint64), ("max_streams", C.c_int32),
                 ("max_batch", C.c_int32), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("user", C.c_void_p), ("cuda_stream", C.c_void_p)]
+
+
+class dibr_tuning(C.Structure):
+    _fields_ = [("ring_slots", C.c_int32), ("ctas_per_sm", C.c_int32), ("load_mode", C.c_int32),
+                ("l2_prefetch", C.c_int32), ("rows_per_unit", C.c_int32)]
 
 
 class dibr_completion(C.Structure):
@@ -105,6 +111,8 @@ def load(build_if_missing=True):
         "dibr_submit_frame": (C.c_int, [ctx, C.c_int, C.c_uint64, P(dibr_image), P(dibr_outputs)]),
         "dibr_poll": (C.c_int, [ctx, P(dibr_completion), C.c_int, P(C.c_int), C.c_int]),
         "dibr_close_stream": (C.c_int, [ctx, C.c_int]),
+        "dibr_set_tuning": (C.c_int, [ctx, P(dibr_tuning)]),
+        "dibr_get_tuning": (C.c_int, [ctx, P(dibr_tuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -182,6 +190,14 @@ def dibr_poll(ctx, comps, max_n, n_out, timeout_us):
 
 def dibr_close_stream(ctx, sid):
     return _fn("dibr_close_stream")(ctx, sid)
+
+
+def dibr_set_tuning(ctx, t):
+    return _fn("dibr_set_tuning")(ctx, C.byref(t))
+
+
+def dibr_get_tuning(ctx, t):
+    return _fn("dibr_get_tuning")(ctx, C.byref(t))
 
 
 # ------------------------------------------------------------------ convenience layer
@@ -313,6 +329,18 @@ class Context:
         n = C.c_int(0)
         st = self.check(dibr_poll(self._ctx, comps, max_n, n, timeout_us))
         return [comps[i] for i in range(n.value)] if st == DIBR_OK else []
+
+    def set_tuning(self, **kw):
+        t = dibr_tuning()
+        dibr_get_tuning(self._ctx, t)
+        for k, v in kw.items():
+            setattr(t, k, v)
+        return self.check(dibr_set_tuning(self._ctx, t))
+
+    def get_tuning(self):
+        t = dibr_tuning()
+        self.check(dibr_get_tuning(self._ctx, t))
+        return {f: getattr(t, f) for f, _ in t._fields_}
 
     def close_stream(self, sid):
         return self.check(dibr_close_stream(self._ctx, sid))
