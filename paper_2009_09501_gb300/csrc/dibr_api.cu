@@ -144,6 +144,24 @@ static void build_tables(const dibr_params *p, int16_t *hL, int16_t *hR, int32_t
   }
 }
 
+namespace dibr {
+// Argument checks of one image (params, input, outputs), for the batch entry points.
+dibr_status check_image_args(const dibr_params *p, const dibr_image *img, const dibr_outputs *o, std::string *why) {
+  dibr_status s = check_params(p, img, why);
+  if (s == DIBR_OK) s = check_outputs(p, img, o, why);
+  return s;
+}
+
+// The kernels' packed tables: lut_h[d] = (hR << 16) | (hL & 0xFFFF); lut_n[d] = 510 * s_L(d).
+void shift_tables(const dibr_params *p, int32_t *lut_h, int32_t *lut_n) {
+  int16_t hL[256], hR[256];
+  build_tables(p, hL, hR, lut_n);
+  for (int d = 0; d < 256; ++d)
+    lut_h[d] = static_cast<int32_t>((static_cast<uint32_t>(static_cast<uint16_t>(hR[d])) << 16) |
+                                    static_cast<uint16_t>(hL[d]));
+}
+}  // namespace dibr
+
 // ---------------------------------------------------------------- launch planning
 static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -317,11 +335,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   a.depth_pitch = o->depth_pitch;
   a.outputs = p->outputs;
   a.warp_mode = p->warp_mode;
-  int16_t hL[256], hR[256];
-  build_tables(p, hL, hR, a.lut_n);
-  for (int d = 0; d < 256; ++d)
-    a.lut_h[d] = static_cast<int32_t>((static_cast<uint32_t>(static_cast<uint16_t>(hR[d])) << 16) |
-                                      static_cast<uint16_t>(hL[d]));
+  shift_tables(p, a.lut_h, a.lut_n);
   cudaError_t e = launch_band(a, smem, per_sm, stream);
   if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
   ++launches;

@@ -329,65 +329,99 @@ __device__ __forceinline__ void store16(uint8_t *p, uint4 v, int npx) {
   }
 }
 
-template <int kMaxThreads, int kMinBlocks>
-__global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
-    band_kernel(const __grid_constant__ BandArgs a) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  const BandSmem L = band_smem_layout(a.nb, a.srow, a.nch, a.depth_src);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.bar);
-  int4 *lut4 = reinterpret_cast<int4 *>(smem + L.lut);  // {-hL, -hR, (255 - d) << 24, 0}
-  uint8_t *ring = smem + L.ring;
-  uint8_t *drow = smem + L.drow;
-  uint32_t *zb0 = reinterpret_cast<uint32_t *>(smem + L.zb);  // [2 rows][L, R][nch*16]
-  int32_t *lut_n = reinterpret_cast<int32_t *>(smem + L.zb);  // literal gather only
+// One image's arguments as the band routine sees them (built from the kernel
+// parameters for a single image, from a descriptor in device memory for a batch).
+struct Job {
+  const uint8_t *in;
+  int64_t in_pitch;
+  const CUtensorMap *tmap;  // tensor-box load modes only
+  const uint8_t *depth_in;
+  int64_t depth_in_pitch;
+  uint8_t *out[O_COUNT];
+  int64_t out_pitch, depth_pitch;
+  int W, H, nch, row_bytes, load_mode, nbox, box_bytes, box_step;
+  uint32_t outputs;
+  int warp_mode, depth_src, l2_prefetch;
+};
 
-  const int tid = threadIdx.x, nc = a.nc, W = a.W, H = a.H, nb = a.nb;
-  const int zlen = a.nch * kChunk;
-  const int ys = static_cast<int>(static_cast<int64_t>(blockIdx.x) * H / a.grid);
-  const int ye = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * H / a.grid);
+// Shared-memory regions of one CTA (laid out for the widest image of the launch).
+struct Shm {
+  uint64_t *full;  // ring-slot mbarriers
+  int4 *lut4;      // {-hL, -hR, (255 - d) << 24, 0} per depth
+  int32_t *lut_n;  // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
+  uint8_t *ring, *drow;
+  uint32_t *zb0;   // [2 rows][L, R][zlen]
+  int nb, srow, zlen;
+};
+
+__device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch_max, int depth_src) {
+  const BandSmem L = band_smem_layout(nb, srow, nch_max, depth_src);
+  Shm m;
+  m.full = reinterpret_cast<uint64_t *>(smem + L.bar);
+  m.lut4 = reinterpret_cast<int4 *>(smem + L.lut);
+  m.ring = smem + L.ring;
+  m.drow = smem + L.drow;
+  m.zb0 = reinterpret_cast<uint32_t *>(smem + L.zb);
+  m.lut_n = reinterpret_cast<int32_t *>(smem + L.zb);
+  m.nb = nb;
+  m.srow = srow;
+  m.zlen = nch_max * kChunk;
+  return m;
+}
+
+// Shift tables into shared memory (all threads; a barrier must follow).
+__device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, const int32_t *lut_n, bool forward) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    const int32_t h = lut_h[i];
+    m.lut4[i] = make_int4(-static_cast<int16_t>(h & 0xFFFF), -(h >> 16),
+                          static_cast<int>((255u - static_cast<uint32_t>(i)) << 24), 0);
+    if (!forward) m.lut_n[i] = lut_n[i];
+  }
+}
+
+// Rows [ys, ye) of one image, every stage of the pipeline (see the file comment).  All
+// threads of the CTA call it together.  kbase counts the ring loads this CTA issued
+// before (the slot and mbarrier phase of a load follow from it); it is advanced by the
+// loads issued here.  Returns false when a bounded wait gave up (the status word is
+// set and the copies in flight have been waited for).
+__device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
+                                         int *status, unsigned long long timeout_ns) {
+  const int tid = threadIdx.x, nc = blockDim.x, W = a.W, H = a.H, nb = m.nb;
   const bool binom = a.depth_src == DS_BINOM5;
   const bool forward = a.warp_mode == DIBR_WARP_FORWARD;
   const int halo = binom ? 2 : 0;
   const int la = max(ys - halo, 0), lb = min(ye + halo, H);
   const int nload = lb - la;
+  const int zimg = a.nch * kChunk;  // this image's targets, rounded up to whole chunks
+  const uint32_t k0 = kbase;
 
-  for (int i = tid; i < 256; i += blockDim.x) {
-    lut4[i] = make_int4(-static_cast<int16_t>(a.lut_h[i] & 0xFFFF), -(a.lut_h[i] >> 16),
-                        static_cast<int>((255u - static_cast<uint32_t>(i)) << 24), 0);
-    if (!forward) lut_n[i] = a.lut_n[i];
-  }
-  if (tid == 0) {
-    for (int i = 0; i < nb; ++i) mbar_init(&full[i], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (ys >= ye) return;
-
-  // Row k = r - la of the CTA's rows goes to slot k % nb.  Warp 0 issues the loads of
-  // rows [issued, upto); the caller guarantees every earlier occupant of those slots
-  // has been released by all threads (a barrier separates the last use from the call).
+  // Row k = r - la of the band is the (k0 + k)-th load of this CTA: slot (k0+k) % nb.
+  // Warp 0 issues the loads of rows [issued, upto); the caller guarantees every
+  // earlier occupant of those slots has been released by all threads (a barrier
+  // separates the last use from the call).
   int issued = 0;
   auto issue_loads = [&](int upto) {
     upto = min(upto, nload);
     if (tid < 32) {
-      if (tid == 0 && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(&a.tmap);
+      if (tid == 0 && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
       for (int k = issued; k < upto; ++k) {
-        const int s = k % nb;
-        uint8_t *dst = ring + s * a.srow;
+        const uint32_t g = k0 + k;
+        const int s = g % nb;
+        uint8_t *dst = m.ring + s * m.srow;
         if (a.load_mode == LM_BULK) {
           if (tid == 0) {
-            mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(a.row_bytes));
+            mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.row_bytes));
             bulk_load(dst, a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes),
-                      &full[s]);
+                      &m.full[s]);
           }
         } else {
-          if (tid == 0) mbar_arrive_expect_tx(&full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
+          if (tid == 0) mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
           __syncwarp();
           for (int i = tid; i < a.nbox; i += 32) {
             if (a.load_mode == LM_T3)
-              tma_load_3d(dst + i * a.box_bytes, &a.tmap, 0, i * a.box_step, la + k, &full[s]);
+              tma_load_3d(dst + i * a.box_bytes, a.tmap, 0, i * a.box_step, la + k, &m.full[s]);
             else
-              tma_load_2d(dst + i * a.box_bytes, &a.tmap, i * a.box_step, la + k, &full[s]);
+              tma_load_2d(dst + i * a.box_bytes, a.tmap, i * a.box_step, la + k, &m.full[s]);
           }
         }
       }
@@ -395,8 +429,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     issued = max(issued, upto);
   };
   issue_loads(nb);
-  // the CTA's rows beyond the ring's first fill go to L2 now, so that every later ring
-  // refill is an L2 hit: the whole input streams from HBM at the start of the launch
+  // optionally, the band's later rows go to L2 now
   if (a.l2_prefetch && tid < 32) {
     if (a.load_mode == LM_BULK) {
       for (int k = nb + tid; k < nload; k += 32)
@@ -404,13 +437,12 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     } else {
       for (int j = tid; j < (nload - nb) * a.nbox; j += 32) {
         const int k = nb + j / a.nbox, i = j % a.nbox;
-        if (a.load_mode == LM_T3) tma_prefetch_3d(&a.tmap, 0, i * a.box_step, la + k);
-        else tma_prefetch_2d(&a.tmap, i * a.box_step, la + k);
+        if (a.load_mode == LM_T3) tma_prefetch_3d(a.tmap, 0, i * a.box_step, la + k);
+        else tma_prefetch_2d(a.tmap, i * a.box_step, la + k);
       }
     }
   }
 
-  // ---------------------------------------------------------------------- consumers
   const int lane = tid & 31;
   const int x0 = tid * kChunk;
   const int npx = max(0, min(kChunk, W - x0));
@@ -418,10 +450,10 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
   const int warp_lo = (tid & ~31) * kChunk;
   const int warp_hi = min(W, warp_lo + 32 * kChunk);
   bool timed_out = false;
-  auto slot = [&](int r) { return ring + ((r - la) % nb) * a.srow; };
+  auto slot = [&](int r) { return m.ring + ((k0 + (r - la)) % nb) * m.srow; };
   auto wait_row = [&](int r) {
-    const int k = r - la;
-    if (!mbar_wait_bounded(&full[k % nb], (k / nb) & 1, a.timeout_ns)) timed_out = true;
+    const uint32_t g = k0 + (r - la);
+    if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, timeout_ns)) timed_out = true;
   };
 
   const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
@@ -449,8 +481,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
   }
 
   for (int y = ys; y < ye && !aborted; ++y) {
-    uint32_t *zl = zb0 + (y & 1) * 2 * zlen;
-    uint32_t *zr = zl + zlen;
+    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
+    uint32_t *zr = zl + m.zlen;
     // ---- phase A: depth of row y in registers; clear this row's z-buffer targets
     uint4 d = make_uint4(0u, 0u, 0u, 0u);
     if (binom) {
@@ -489,14 +521,14 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     if (active && want_depth)
       store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d, npx);
     if (forward) {
-      if (active) *reinterpret_cast<uint4 *>(drow + x0) = d;
+      if (active) *reinterpret_cast<uint4 *>(m.drow + x0) = d;
       // clear this warp's 512 targets of both views, consecutive lanes on consecutive
       // 16-byte words (no bank conflicts)
       const uint4 e = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int t = warp_lo + 4 * (32 * q + lane);
-        if (t < zlen) {
+        if (t < zimg) {
           *reinterpret_cast<uint4 *>(zl + t) = e;
           *reinterpret_cast<uint4 *>(zr + t) = e;
         }
@@ -519,8 +551,8 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
       const uint32_t ob = 3u * static_cast<uint32_t>(xb);
       const uint32_t cws = smem_addr(rgbrow) + (ob & ~3u);  // the lane's colours: +96 bytes per step
       const uint32_t sh = (ob & 3u) * 8u;
-      const uint32_t ds = smem_addr(drow) + static_cast<uint32_t>(xb);
-      const uint32_t ls = smem_addr(lut4);
+      const uint32_t ds = smem_addr(m.drow) + static_cast<uint32_t>(xb);
+      const uint32_t ls = smem_addr(m.lut4);
       const uint32_t zls = smem_addr(zl), zrs = smem_addr(zr);
       const bool full_warp = warp_hi - warp_lo == 32 * kChunk;
 #pragma unroll 4
@@ -549,7 +581,7 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
 #pragma unroll
       for (int i = 0; i < kChunk; ++i) {
         const int x = min(x0 + i, W - 1);
-        const int n = lut_n[bsel(dw, i)];
+        const int n = m.lut_n[bsel(dw, i)];
         int sl = (510 * x + n) / 510, sr = (510 * x - n) / 510;
         if (static_cast<unsigned>(sl) >= static_cast<unsigned>(W)) sl = x;
         if (static_cast<unsigned>(sr) >= static_cast<unsigned>(W)) sr = x;
@@ -599,25 +631,97 @@ __global__ void __launch_bounds__(kMaxThreads, kMinBlocks)
     }
   }
 
-  if (aborted && tid == 0) {
-    atomicOr(a.status, ST_TIMEOUT_FULL);
-    // let every copy already issued land before the CTA's shared memory goes away
-    for (int k = max(0, issued - nb); k < issued; ++k)
-      if (!mbar_wait_bounded(&full[k % nb], (k / nb) & 1, a.timeout_ns)) atomicOr(a.status, ST_TIMEOUT_DRAIN);
+  kbase = k0 + issued;
+  if (aborted) {
+    if (tid == 0) {
+      atomicOr(status, ST_TIMEOUT_FULL);
+      // let every copy already issued land before the CTA's shared memory goes away
+      for (int k = max(0, issued - nb); k < issued; ++k) {
+        const uint32_t g = k0 + k;
+        if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, timeout_ns)) atomicOr(status, ST_TIMEOUT_DRAIN);
+      }
+    }
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// One image: CTA b owns the rows [b*H/grid, (b+1)*H/grid).
+__global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const Shm m = carve(smem, a.nb, a.srow, a.nch, a.depth_src);
+  fill_luts(m, a.lut_h, a.lut_n, a.warp_mode == DIBR_WARP_FORWARD);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.nb; ++i) mbar_init(&m.full[i], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int ys = static_cast<int>(static_cast<int64_t>(blockIdx.x) * a.H / a.grid);
+  const int ye = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * a.H / a.grid);
+  if (ys >= ye) return;
+  Job j;
+  j.in = a.in;
+  j.in_pitch = a.in_pitch;
+  j.tmap = &a.tmap;
+  j.depth_in = a.depth_in;
+  j.depth_in_pitch = a.depth_in_pitch;
+#pragma unroll
+  for (int i = 0; i < O_COUNT; ++i) j.out[i] = a.out[i];
+  j.out_pitch = a.out_pitch;
+  j.depth_pitch = a.depth_pitch;
+  j.W = a.W; j.H = a.H; j.nch = a.nch; j.row_bytes = a.row_bytes; j.load_mode = a.load_mode;
+  j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
+  j.outputs = a.outputs; j.warp_mode = a.warp_mode; j.depth_src = a.depth_src; j.l2_prefetch = a.l2_prefetch;
+  uint32_t kbase = 0;
+  run_band(j, m, ys, ye, kbase, a.status, a.timeout_ns);
+}
+
+// ---------------------------------------------------------------------------------
+// A batch of images in one persistent launch: CTAs pull work units (an image and a
+// range of its rows) from a device counter until none is left.
+__global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, DS_BINOM5).flags);
+  const Shm m = carve(smem, b.nb, b.srow, b.nch_max, DS_BINOM5);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < b.nb; ++i) mbar_init(&m.full[i], 1);
+    fence_mbar_init();
+  }
+  uint32_t kbase = 0;
+  while (true) {
+    __syncthreads();  // the previous unit is done with the ring, tables and unit_s
+    if (threadIdx.x == 0) *unit_s = atomicAdd(b.counter, 1);
+    __syncthreads();
+    const int u = *unit_s;
+    if (u >= b.n_units) break;
+    const int4 un = b.units[u];  // {image, first row, end row}
+    const ImageDesc &dsc = b.descs[un.x];
+    Job j;
+    j.in = dsc.in;
+    j.in_pitch = dsc.in_pitch;
+    j.tmap = nullptr;
+    j.depth_in = dsc.depth_in;
+    j.depth_in_pitch = dsc.depth_in_pitch;
+#pragma unroll
+    for (int i = 0; i < O_COUNT; ++i) j.out[i] = dsc.out[i];
+    j.out_pitch = dsc.out_pitch;
+    j.depth_pitch = dsc.depth_pitch;
+    j.W = dsc.W; j.H = dsc.H; j.nch = dsc.nch; j.row_bytes = dsc.row_bytes; j.load_mode = LM_BULK;
+    j.nbox = 1; j.box_bytes = dsc.row_bytes; j.box_step = 0;
+    j.outputs = dsc.outputs; j.warp_mode = dsc.warp_mode; j.depth_src = dsc.depth_src; j.l2_prefetch = 0;
+    fill_luts(m, dsc.lut_h, dsc.lut_n, j.warp_mode == DIBR_WARP_FORWARD);
+    __syncthreads();
+    if (!run_band(j, m, un.y, un.z, kbase, b.status, b.timeout_ns)) break;
   }
 }
 
-template <int T, int B>
-cudaError_t launch_variant(const BandArgs &a, int smem_bytes, cudaStream_t st) {
-  static bool attr_set = false;  // per process; the attribute is per function
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(band_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  band_kernel<T, B><<<a.grid, a.nc, smem_bytes, st>>>(a);
-  return cudaGetLastError();
+template <typename K>
+cudaError_t allow_smem(K kernel, bool &done) {
+  if (done) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) done = true;
+  return e;
 }
 
 }  // namespace
@@ -626,7 +730,19 @@ int band_max_threads(int ctas_per_sm) { return ctas_per_sm >= 2 ? 256 : kMaxCons
 
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
   (void)ctas_per_sm;
-  return launch_variant<kMaxConsumers, 1>(a, smem_bytes, st);
+  static bool done = false;  // per process: the attribute is per function
+  cudaError_t e = allow_smem(band_kernel, done);
+  if (e != cudaSuccess) return e;
+  band_kernel<<<a.grid, a.nc, smem_bytes, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, cudaStream_t st) {
+  static bool done = false;
+  cudaError_t e = allow_smem(batch_kernel, done);
+  if (e != cudaSuccess) return e;
+  batch_kernel<<<grid, b.nc, smem_bytes, st>>>(b);
+  return cudaGetLastError();
 }
 
 }  // namespace dibr

@@ -1,5 +1,16 @@
-// dibr_batch.cu -- batched synthesis of images of uneven sizes.
+// dibr_batch.cu -- images of uneven sizes in one persistent launch (dibr_synthesize_batch,
+// dibr_enqueue_batch).
+//
+// Each image is cut into work units of rows_per_unit rows.  The host writes one
+// descriptor per image (pointers, sizes, shift tables) and the unit list, largest images
+// first, into device memory with a single copy; the persistent CTAs of the batch kernel
+// take units from a device counter until none is left, so the launch balances itself
+// over images of any mix of sizes.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
 #include <string>
+#include <vector>
 
 #include "dibr.h"
 #include "dibr_context.h"
@@ -7,36 +18,293 @@
 
 using namespace dibr;
 
+namespace dibr {
+dibr_status check_image_args(const dibr_params *p, const dibr_image *img, const dibr_outputs *o,
+                             std::string *why);
+void shift_tables(const dibr_params *p, int32_t *lut_h, int32_t *lut_n);
+}  // namespace dibr
+
 void dibr_ctx::release_batch_buffers() {
   for (DevBuf *b : {&batch_desc, &batch_img, &batch_depth}) {
     dev_free(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;
   }
+  if (batch_pinned) {
+    if (batch_copy_done) cudaEventSynchronize(batch_copy_done);
+    cudaFreeHost(batch_pinned);
+    batch_pinned = nullptr;
+    batch_pinned_bytes = 0;
+  }
+  if (batch_copy_done) {
+    cudaEventDestroy(batch_copy_done);
+    batch_copy_done = nullptr;
+  }
+}
+
+// All buffers in device memory.  Enqueues the batch on the context's stream.
+dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                                           const dibr_outputs *outs) {
+  if (n == 0) return DIBR_OK;
+  const int rows_per_unit = tuning.rows_per_unit > 0 ? tuning.rows_per_unit : 32;
+  // --- inputs that a bulk row copy cannot read directly are repacked (16-byte rows)
+  std::vector<const uint8_t *> in(n);
+  std::vector<int64_t> in_pitch(n);
+  std::vector<int> row_bytes(n);
+  size_t realign_bytes = 0, depth_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    const dibr_image &im = imgs[i];
+    const bool ok = (reinterpret_cast<uintptr_t>(im.rgb) & 15u) == 0 && (im.pitch & 15) == 0 && (3 * im.width) % 16 == 0;
+    if (!ok) realign_bytes += static_cast<size_t>(round_up(3 * im.width, 16)) * im.height;
+    if (p[n_params == 1 ? 0 : i].depth_rule == DIBR_DEPTH_LUMA_XBF)
+      depth_bytes += static_cast<size_t>(round_up(im.width, 16)) * im.height;
+  }
+  dibr_status s;
+  if (realign_bytes && (s = ensure(batch_img, realign_bytes)) != DIBR_OK) return s;
+  if (depth_bytes && (s = ensure(batch_depth, depth_bytes)) != DIBR_OK) return s;
+  size_t ro = 0, dof = 0;
+  std::vector<const uint8_t *> depth_in(n, nullptr);
+  std::vector<int64_t> depth_pitch_in(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const dibr_image &im = imgs[i];
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    const bool ok = (reinterpret_cast<uintptr_t>(im.rgb) & 15u) == 0 && (im.pitch & 15) == 0 && (3 * im.width) % 16 == 0;
+    if (ok) {
+      in[i] = im.rgb;
+      in_pitch[i] = im.pitch;
+      row_bytes[i] = 3 * im.width;
+    } else {
+      const int64_t ap = round_up(3 * im.width, 16);
+      uint8_t *dst = batch_img.ptr + ro;
+      cudaError_t e = cudaMemcpy2DAsync(dst, ap, im.rgb, im.pitch, 3 * static_cast<size_t>(im.width), im.height,
+                                        cudaMemcpyDeviceToDevice, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "repacking a batch input");
+      in[i] = dst;
+      in_pitch[i] = ap;
+      row_bytes[i] = static_cast<int>(ap);  // whole 16-byte units; the padding is never used
+      ro += static_cast<size_t>(ap) * im.height;
+    }
+    if (pp.depth_rule == DIBR_DEPTH_LUMA_XBF) {
+      const int64_t dp = round_up(im.width, 16);
+      uint8_t *dd = batch_depth.ptr + dof;
+      cudaError_t e = launch_xbf(in[i], in_pitch[i], im.width, im.height, pp.xbf_radius, pp.xbf_sigma_s,
+                                 pp.xbf_sigma_r, dd, dp, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cross-bilateral launch");
+      ++launches;
+      depth_in[i] = dd;
+      depth_pitch_in[i] = dp;
+      dof += static_cast<size_t>(dp) * im.height;
+    }
+  }
+  // --- shared-memory plan for the widest image
+  int nch_max = 1, srow = 128;
+  for (int i = 0; i < n; ++i) {
+    const int nch = (imgs[i].width + kChunk - 1) / kChunk;
+    nch_max = std::max(nch_max, nch);
+    srow = std::max(srow, round_up(std::max(row_bytes[i], 48 * nch), 128));
+  }
+  const int nc = round_up(nch_max, 32);
+  const int max_per = std::max(1, std::min(65536 / (nc * 128), 2048 / nc));
+  auto per_for = [&](int nb) {
+    const int tot = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
+    if (tot > max_smem) return 0;
+    int per = std::min(max_per, smem_per_sm / (tot + 1024));
+    if (tuning.ctas_per_sm > 0) per = std::min(per, tuning.ctas_per_sm);
+    return per;
+  };
+  const int max_nb = tuning.ring_slots > 0 ? std::max(4, std::min(kMaxRing, tuning.ring_slots)) : kMaxRing;
+  int best = 0, nb = 4;
+  for (int k = 4; k <= max_nb; ++k) best = std::max(best, per_for(k));
+  if (best < 1) {
+    set_error("batch images too wide for shared memory");
+    return DIBR_E_INVALID;
+  }
+  for (int k = 4; k <= max_nb; ++k)
+    if (per_for(k) == best) nb = k;
+  const int smem = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
+
+  // --- descriptors and units (largest images first), staged in pinned memory
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return static_cast<int64_t>(imgs[a].width) * imgs[a].height > static_cast<int64_t>(imgs[b].width) * imgs[b].height;
+  });
+  int n_units = 0;
+  for (int i = 0; i < n; ++i) n_units += (imgs[i].height + rows_per_unit - 1) / rows_per_unit;
+  // [counter][pad] [descs] [units]: every part 256-byte aligned (the kernel reads the
+  // units as int4 and the descriptors' 64-bit fields)
+  const size_t off_desc = 256;
+  const size_t off_units = (off_desc + sizeof(ImageDesc) * n + 255) / 256 * 256;
+  const size_t total = off_units + sizeof(int4) * static_cast<size_t>(n_units);
+  if (batch_copy_done) cudaEventSynchronize(batch_copy_done);  // the previous copy has read the staging
+  if (batch_pinned_bytes < total) {
+    if (batch_pinned) cudaFreeHost(batch_pinned);
+    batch_pinned = nullptr;
+    batch_pinned_bytes = 0;
+    if (cudaHostAlloc(reinterpret_cast<void **>(&batch_pinned), total, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned allocation of %zu bytes failed", total);
+      return DIBR_E_NOMEM;
+    }
+    batch_pinned_bytes = total;
+  }
+  if (!batch_copy_done && cudaEventCreateWithFlags(&batch_copy_done, cudaEventDisableTiming) != cudaSuccess)
+    return DIBR_E_CUDA;
+  if ((s = ensure(batch_desc, total)) != DIBR_OK) return s;
+  std::memset(batch_pinned, 0, off_desc);
+  ImageDesc *descs = reinterpret_cast<ImageDesc *>(batch_pinned + off_desc);
+  int4 *units = reinterpret_cast<int4 *>(batch_pinned + off_units);
+  int u = 0;
+  for (int oi = 0; oi < n; ++oi) {
+    const int i = order[oi];
+    const dibr_image &im = imgs[i];
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    const dibr_outputs &o = outs[i];
+    ImageDesc &d = descs[i];
+    std::memset(&d, 0, sizeof(d));
+    d.in = in[i];
+    d.in_pitch = in_pitch[i];
+    d.depth_in = depth_in[i];
+    d.depth_in_pitch = depth_pitch_in[i];
+    d.out[O_ANA] = o.anaglyph;
+    d.out[O_LEFT] = o.left;
+    d.out[O_RIGHT] = o.right;
+    d.out[O_HSBS] = o.hsbs;
+    d.out[O_DEPTH] = o.depth;
+    d.out_pitch = o.pitch;
+    d.depth_pitch = o.depth_pitch;
+    d.W = im.width;
+    d.H = im.height;
+    d.nch = (im.width + kChunk - 1) / kChunk;
+    d.row_bytes = row_bytes[i];
+    d.outputs = pp.outputs;
+    d.warp_mode = pp.warp_mode;
+    d.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : pp.depth_rule == DIBR_DEPTH_LUMA ? DS_LUMA : DS_GLOBAL;
+    shift_tables(&pp, d.lut_h, d.lut_n);
+    for (int y0 = 0; y0 < im.height; y0 += rows_per_unit) units[u++] = make_int4(i, y0, std::min(im.height, y0 + rows_per_unit), 0);
+  }
+  cudaError_t e = cudaMemcpyAsync(batch_desc.ptr, batch_pinned, total, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(batch_copy_done, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+  BatchArgs b;
+  b.descs = reinterpret_cast<const ImageDesc *>(batch_desc.ptr + off_desc);
+  b.units = reinterpret_cast<const int4 *>(batch_desc.ptr + off_units);
+  b.n_units = n_units;
+  b.counter = reinterpret_cast<int *>(batch_desc.ptr);
+  b.status = status_dev;
+  b.timeout_ns = timeout_ns;
+  b.nb = nb;
+  b.srow = srow;
+  b.nch_max = nch_max;
+  b.nc = nc;
+  const int grid = std::max(1, std::min(n_units, num_sms * best));
+  e = launch_batch(b, grid, smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+  ++launches;
+  return DIBR_OK;
+}
+
+static dibr_status check_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                               const dibr_outputs *outs) {
+  if (!c || n < 0 || (n > 0 && (!imgs || !p || !outs))) return DIBR_E_INVALID;
+  if (n > 0 && n_params != 1 && n_params != n) {
+    c->set_error("n_params must be 1 or n");
+    return DIBR_E_INVALID;
+  }
+  if (n > c->max_batch) {
+    c->set_error("batch of %d images exceeds max_batch %d", n, c->max_batch);
+    return DIBR_E_INVALID;
+  }
+  for (int i = 0; i < n; ++i) {
+    std::string why;
+    const dibr_status s = check_image_args(&p[n_params == 1 ? 0 : i], &imgs[i], &outs[i], &why);
+    if (s != DIBR_OK) {
+      c->set_error("image %d: %s", i, why.c_str());
+      return s;
+    }
+  }
+  return DIBR_OK;
 }
 
 extern "C" {
 
-dibr_status dibr_enqueue_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p,
-                               int n_params, const dibr_outputs *outs) {
-  if (!c || n < 0 || (n > 0 && (!imgs || !p || !outs))) return DIBR_E_INVALID;
-  if (n_params != 1 && n_params != n) return DIBR_E_INVALID;
-  for (int i = 0; i < n; ++i) {
-    dibr_status s = dibr_enqueue_image(c, &imgs[i], &p[n_params == 1 ? 0 : i], &outs[i]);
-    if (s != DIBR_OK) return s;
-  }
-  return DIBR_OK;
+dibr_status dibr_enqueue_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                               const dibr_outputs *outs) {
+  dibr_status s = check_batch(c, n, imgs, p, n_params, outs);
+  if (s != DIBR_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if (!imgs[i].on_device || !outs[i].on_device) {
+      c->set_error("dibr_enqueue_batch needs device buffers");
+      return DIBR_E_INVALID;
+    }
+  cudaSetDevice(c->device);
+  return c->enqueue_batch_device(n, imgs, p, n_params, outs);
 }
 
-dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p,
-                                  int n_params, const dibr_outputs *outs) {
-  if (!c || n < 0 || (n > 0 && (!imgs || !p || !outs))) return DIBR_E_INVALID;
-  if (n_params != 1 && n_params != n) return DIBR_E_INVALID;
+dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                                  const dibr_outputs *outs) {
+  dibr_status s = check_batch(c, n, imgs, p, n_params, outs);
+  if (s != DIBR_OK) return s;
+  cudaSetDevice(c->device);
+  // host buffers are staged through one device area: inputs, then outputs
+  std::vector<dibr_image> di(imgs, imgs + n);
+  std::vector<dibr_outputs> dout(outs, outs + n);
+  size_t need = 0;
+  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
   for (int i = 0; i < n; ++i) {
-    dibr_status s = dibr_synthesize_image(c, &imgs[i], &p[n_params == 1 ? 0 : i], &outs[i]);
-    if (s != DIBR_OK) return s;
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    if (!imgs[i].on_device) need += static_cast<size_t>(round_up(3 * imgs[i].width, 16)) * imgs[i].height;
+    if (!outs[i].on_device)
+      for (int k = 0; k < O_COUNT; ++k)
+        if (pp.outputs & bits[k])
+          need += static_cast<size_t>(round_up(k == O_DEPTH ? imgs[i].width : 3 * imgs[i].width, 16)) * imgs[i].height;
   }
-  return DIBR_OK;
+  if (need && (s = c->ensure(c->stage_in, need)) != DIBR_OK) return s;
+  size_t off = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    const int W = imgs[i].width, H = imgs[i].height;
+    if (!imgs[i].on_device) {
+      const int64_t ap = round_up(3 * W, 16);
+      e = cudaMemcpy2DAsync(c->stage_in.ptr + off, ap, imgs[i].rgb, imgs[i].pitch, 3 * static_cast<size_t>(W), H,
+                            cudaMemcpyHostToDevice, c->stream);
+      di[i].rgb = c->stage_in.ptr + off;
+      di[i].pitch = ap;
+      di[i].on_device = 1;
+      off += static_cast<size_t>(ap) * H;
+    }
+    if (!outs[i].on_device) {
+      uint8_t **dp[O_COUNT] = {&dout[i].anaglyph, &dout[i].left, &dout[i].right, &dout[i].hsbs, &dout[i].depth};
+      const int64_t op = round_up(3 * W, 16), dpp = round_up(W, 16);
+      for (int k = 0; k < O_COUNT; ++k) {
+        if (!(pp.outputs & bits[k])) continue;
+        *dp[k] = c->stage_in.ptr + off;
+        off += static_cast<size_t>(k == O_DEPTH ? dpp : op) * H;
+      }
+      dout[i].pitch = op;
+      dout[i].depth_pitch = dpp;
+      dout[i].on_device = 1;
+    }
+  }
+  if (e != cudaSuccess) return c->cuda_fail(e, "batch input upload");
+  if ((s = c->enqueue_batch_device(n, di.data(), p, n_params, dout.data())) != DIBR_OK) return s;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    if (outs[i].on_device) continue;
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    const int W = imgs[i].width, H = imgs[i].height;
+    const uint8_t *src[O_COUNT] = {dout[i].anaglyph, dout[i].left, dout[i].right, dout[i].hsbs, dout[i].depth};
+    uint8_t *dst[O_COUNT] = {outs[i].anaglyph, outs[i].left, outs[i].right, outs[i].hsbs, outs[i].depth};
+    for (int k = 0; k < O_COUNT && e == cudaSuccess; ++k) {
+      if (!(pp.outputs & bits[k])) continue;
+      const bool dep = k == O_DEPTH;
+      e = cudaMemcpy2DAsync(dst[k], dep ? outs[i].depth_pitch : outs[i].pitch, src[k],
+                            dep ? dout[i].depth_pitch : dout[i].pitch, dep ? W : 3 * static_cast<size_t>(W), H,
+                            cudaMemcpyDeviceToHost, c->stream);
+    }
+  }
+  if (e != cudaSuccess) return c->cuda_fail(e, "batch output download");
+  return c->read_status();
 }
 
 }  // extern "C"

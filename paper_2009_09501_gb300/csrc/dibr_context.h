@@ -49,7 +49,9 @@ struct dibr_ctx {
 
   // batched launches (dibr_batch.cu)
   dibr::DevBuf batch_desc, batch_img, batch_depth;
-  std::vector<uint8_t> batch_host;
+  uint8_t *batch_pinned = nullptr;         // descriptor staging (pinned host memory)
+  size_t batch_pinned_bytes = 0;
+  cudaEvent_t batch_copy_done = nullptr;   // the last descriptor upload has read the staging
 
   // serving loop (dibr_serve.cu)
   dibr::ServeState *serve = nullptr;
@@ -64,6 +66,8 @@ struct dibr_ctx {
   dibr_status encode_input(dibr::BandArgs &a, const uint8_t *dev_rgb, int64_t pitch);
   dibr_status enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
   dibr_status synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
+  dibr_status enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                                   const dibr_outputs *outs);
   dibr_status read_status();
   void release_buffers();
   void release_batch_buffers();

@@ -81,8 +81,8 @@ __host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, 
   (void)depth_src;
   BandSmem s;
   s.bar = 0;                       // full[kMaxRing] mbarriers
-  s.flags = 8 * kMaxRing;          // reserved
-  s.lut = s.flags;                 // int4 lut[256]: {-hL[d], -hR[d], (255 - d) << 24, 0}
+  s.flags = 8 * kMaxRing;          // batched launches: the current work unit
+  s.lut = s.flags + 64;            // int4 lut[256]: {-hL[d], -hR[d], (255 - d) << 24, 0}
   s.ring = round_up(s.lut + 4096, 128);
   // depth of the current row, one byte per column (read back by the scatter)
   s.drow = round_up(s.ring + nb * srow, 16);
@@ -94,8 +94,38 @@ __host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, 
   return s;
 }
 
+// One image of a batched launch, in device memory.
+struct alignas(16) ImageDesc {
+  const uint8_t *in;
+  int64_t in_pitch;
+  const uint8_t *depth_in;
+  int64_t depth_in_pitch;
+  uint8_t *out[O_COUNT];
+  int64_t out_pitch, depth_pitch;
+  int32_t W, H, nch, row_bytes;
+  uint32_t outputs;
+  int32_t warp_mode, depth_src, pad;
+  int32_t lut_h[256];
+  int32_t lut_n[256];
+};
+
+static_assert(sizeof(ImageDesc) % 16 == 0, "descriptors are read as an array");
+
+// Arguments of the batched kernel: descriptors, work units {image, first row, end row,
+// 0} in the order they are handed out, and the counter the CTAs take units from.
+struct BatchArgs {
+  const ImageDesc *descs;
+  const int4 *units;
+  int32_t n_units;
+  int *counter;
+  int *status;
+  unsigned long long timeout_ns;
+  int32_t nb, srow, nch_max, nc;
+};
+
 // Host launchers (dibr_band.cu, dibr_xbf.cu).
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st);
+cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, cudaStream_t st);
 int band_max_threads(int ctas_per_sm);
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,

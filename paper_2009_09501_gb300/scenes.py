@@ -38,29 +38,43 @@ def _mix(z):
         return z ^ (z >> np.uint64(31))
 
 
-def _hash(*keys):
-    """Hash a tuple of integer scalars / broadcastable integer arrays to uint64."""
-    h = np.uint64(0x6A09E667F3BCC909)
+def _mix_int(z):
+    """The same finaliser on a Python integer."""
+    m = 0xFFFFFFFFFFFFFFFF
+    z = (z + 0x9E3779B97F4A7C15) & m
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def _key(*keys):
+    """Fold integer scalars into one 64-bit stream key."""
+    h = 0x6A09E667F3BCC909
     for k in keys:
-        k = np.asarray(k).astype(np.uint64)
-        h = _mix(h ^ k)
+        h = _mix_int(h ^ (int(k) & 0xFFFFFFFFFFFFFFFF))
     return h
+
+
+def _hash(key, idx):
+    """Counter-based hash: one SplitMix64 round of (stream key + element counter)."""
+    with np.errstate(over="ignore"):
+        return _mix(np.uint64(key) + np.asarray(idx).astype(np.uint64))
 
 
 def _uniform01(h):
     return (h >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def _gauss(*keys):
-    """Standard normal samples by Box-Muller from two hashed uniforms."""
-    u1 = _uniform01(_hash(*keys, 0))
-    u2 = _uniform01(_hash(*keys, 1))
-    u1 = np.maximum(u1, 1e-300)
-    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+def _gauss(key, idx):
+    """Standard normal samples by Box-Muller from the two 32-bit halves of one hash."""
+    h = _hash(key, idx)
+    u1 = ((h >> np.uint64(40)).astype(np.float32) + np.float32(0.5)) * np.float32(1.0 / 16777216.0)
+    u2 = ((h & np.uint64(0xFFFFFF)).astype(np.float32)) * np.float32(1.0 / 16777216.0)
+    return np.sqrt(np.float32(-2.0) * np.log(u1)) * np.cos(np.float32(2.0 * np.pi) * u2)
 
 
 def _scalar_u(seed, *keys):
-    return float(_uniform01(_hash(seed, _TAG_OBJ, *keys)))
+    return float(_uniform01(_hash(_key(seed, _TAG_OBJ, *keys), 0)))
 
 
 def _scalar_int(seed, lo, hi, *keys):
@@ -119,10 +133,8 @@ class Scene:
                 for oy in ((0.0, -H, H) if self.moving else (0.0,)):
                     self._paint(img, i, o, cx + ox, cy + oy, ax, ay)
         if self.moving:
-            yy, xx = np.mgrid[0:H, 0:W]
-            for c in range(3):
-                n = _gauss(s, _TAG_FRAME, k, yy, xx, c) * 2.0
-                img[:, :, c] = np.clip(np.rint(img[:, :, c] + n), 0, 255).astype(np.uint8)
+            n = _gauss(_key(s, _TAG_FRAME, k), np.arange(H * W * 3, dtype=np.uint64)).reshape(H, W, 3)
+            img[:] = np.clip(np.rint(img + n * np.float32(2.0)), 0, 255).astype(np.uint8)
         return img
 
     def _paint(self, img, i, o, cx, cy, ax, ay):
@@ -141,18 +153,21 @@ class Scene:
         if not mask.any():
             return
         # texture coordinates are local to the object so the texture moves with it
-        lx = (xx - int(np.floor(cx - ax))).astype(np.int64)
-        ly = (yy - int(np.floor(cy - ay))).astype(np.int64)
+        lx = (xx[mask] - int(np.floor(cx - ax))).astype(np.int64)
+        ly = (yy[mask] - int(np.floor(cy - ay))).astype(np.int64)
+        # texture counter: local (x, y, channel) inside a 2^16 x 2^16 object frame
+        cnt = ((ly & 0xFFFF) << 18) | ((lx & 0xFFFF) << 2)
         region = img[by0:by1, bx0:bx1]
         for c in range(3):
+            key = _key(s, _TAG_TEX, i)
             if self.texture == "uniform32":
-                u = _uniform01(_hash(s, _TAG_TEX, i, lx, ly, c))
+                u = _uniform01(_hash(key, cnt | c))
                 n = np.floor(u * 65.0) - 32.0
             else:
-                n = np.rint(_gauss(s, _TAG_TEX, i, lx, ly, c) * 8.0)
+                n = np.rint(_gauss(key, cnt | c) * np.float32(8.0))
             v = np.clip(o["color"][c] + n, 0, 255).astype(np.uint8)
             ch = region[:, :, c]
-            ch[mask] = v[mask]
+            ch[mask] = v
 
 
 def config_scene(index, frame=0):
