@@ -187,6 +187,33 @@ dibr_status dibr_synthesize_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
 dibr_status dibr_enqueue_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
                                const dibr_params *p, int n_params, const dibr_outputs *outs);
 
+/* Batched synthesis that allocates nothing.  The paper has no counterpart: this serves
+ * callers that may not allocate memory at the time they call, for example an application
+ * that reserves its whole device-memory budget at start-up and forbids allocation later,
+ * or code that runs under another framework's memory manager and must not allocate behind
+ * its back.  dibr_synthesize_batch needs a context, and creating one allocates; this entry
+ * point needs none.  It calls no cudaMalloc, cudaFree or other allocating routine: the
+ * small device scratch of the batched launch (a work counter, one descriptor per image, the
+ * list of work units) lives in one fixed array of 267,008 bytes in the library's device
+ * data, which every GPU that loads the library holds until the process exits.
+ *   - Inputs and outputs: device memory of the current device, as for dibr_enqueue_batch.
+ *     Input rows must be whole 16-byte units: 16-byte aligned base and pitch, 3*width a
+ *     multiple of 16 (other images would need a repacking buffer).
+ *   - Limits: 1..64 images; depth rules DIBR_DEPTH_LUMA and DIBR_DEPTH_LUMA_BINOM5 only
+ *     (the cross-bilateral rule needs a depth buffer); at most 8192 work units (rows per
+ *     unit grow to fit).  Anything beyond returns DIBR_E_INVALID, with no error text.
+ *   - cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).  The call
+ *     returns when the batch is done; DIBR_E_TIMEOUT reports a bounded device-side wait
+ *     that gave up.
+ *   - The first call on a device does a one-time set-up on that device (it looks up the
+ *     device address of the scratch array); make that first call before any stream
+ *     capture.
+ *   - Every call shares the scratch array, and each call rewrites it: calls that overlap on
+ *     the GPU (on different streams, or from different threads without ordering) race and
+ *     must not be made; host-side calls are serialised by a mutex. */
+dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const dibr_params *p,
+                                         int n_params, const dibr_outputs *outs, void *cuda_stream);
+
 /* Launch tuning: the knobs an autotuner sweeps (the paper has no counterpart; these
  * change speed, never results).  A zero field means "automatic".
  *   ring_slots     input rows staged in shared memory per CTA, 4..8;

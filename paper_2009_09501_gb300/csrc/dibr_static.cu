@@ -1,0 +1,206 @@
+// dibr_static.cu -- dibr_synthesize_batch_static: the batched synthesis for callers that
+// must not allocate memory.
+//
+// The batch kernel needs a little device memory beside the caller's images: a work
+// counter, one descriptor per image and the list of work units.  dibr_synthesize_batch
+// takes it from a context, which allocates.  This entry point instead uses one array in
+// the library's own device data (file-scope, fixed size), so it needs no context and
+// calls no allocation routine: no cudaMalloc, no cudaFree, no pinned or pageable host
+// allocation.  The descriptors are written into a fixed host array and copied to the
+// device array before the launch.
+#include <cstring>
+#include <mutex>
+
+#include "dibr.h"
+#include "dibr_internal.h"
+
+namespace dibr {
+void shift_tables(const dibr_params *p, int32_t *lut_h, int32_t *lut_n);
+}
+
+using namespace dibr;
+
+namespace {
+
+constexpr int kStaticMaxImages = 64;
+constexpr int kStaticMaxUnits = 8192;
+constexpr int kStaticMaxDevices = 64;
+constexpr size_t kDescOff = 256;  // [counter][status] ... [descriptors] [units]
+constexpr size_t kUnitsOff = (kDescOff + sizeof(ImageDesc) * kStaticMaxImages + 255) / 256 * 256;
+constexpr size_t kStaticBytes = kUnitsOff + sizeof(int4) * kStaticMaxUnits;  // 267,008 bytes
+
+// Device scratch shared by every call on a device (each GPU that loads the library holds
+// it until the process exits).  Host code must not use its name as an address: the
+// device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) uint8_t g_scratch[kStaticBytes];
+
+// Host staging of the descriptors, guarded by g_mu.
+static uint8_t g_staging[kStaticBytes];
+static std::mutex g_mu;
+
+struct DeviceSetup {
+  bool done = false;
+  uint8_t *scratch = nullptr;  // device address of g_scratch on this device
+  int sms = 0, smem_per_sm = 0, max_smem = 0;
+};
+static DeviceSetup g_dev[kStaticMaxDevices];
+
+// Once per device, with that device current: the scratch array's device address and the
+// device limits the launch plan needs.
+dibr_status setup_device(int dev) {
+  DeviceSetup &d = g_dev[dev];
+  if (d.done) return DIBR_OK;
+  void *ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return DIBR_E_CUDA;
+  }
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&d.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DIBR_E_CUDA;
+  }
+  if (!(major == 10 && minor == 3)) return DIBR_E_CUDA;  // built for sm_103a only
+  d.scratch = static_cast<uint8_t *>(ptr);
+  d.done = true;
+  return DIBR_OK;
+}
+
+// Argument checks without any allocation (status codes only).
+bool valid_image(const dibr_params *p, const dibr_image *im, const dibr_outputs *o) {
+  if (!p || !im || !o) return false;
+  if (p->depth_rule != DIBR_DEPTH_LUMA && p->depth_rule != DIBR_DEPTH_LUMA_BINOM5) return false;
+  if (p->disparity_rule < 0 || p->disparity_rule > 1 || p->warp_mode < 0 || p->warp_mode > 1) return false;
+  if (p->warp_mode == DIBR_WARP_GATHER_FIG3 && p->disparity_rule != DIBR_DISP_PAPER) return false;
+  if (p->max_parallax_px < 0 || p->max_parallax_px > 1024 || p->threshold < 0 || p->threshold > 255) return false;
+  const uint32_t all = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS | DIBR_OUT_DEPTH;
+  if (p->outputs == 0 || (p->outputs & ~all)) return false;
+  if (!im->rgb || !im->on_device || !o->on_device) return false;
+  if (im->width < 1 || im->height < 1 || im->width > kMaxWidth || im->height > 65535) return false;
+  if (im->pitch < 3 * static_cast<int64_t>(im->width)) return false;
+  // rows are read with one bulk copy each: 16-byte aligned rows of whole 16-byte units
+  if ((reinterpret_cast<uintptr_t>(im->rgb) & 15u) || (im->pitch & 15) || (3 * im->width) % 16) return false;
+  if ((p->outputs & DIBR_OUT_HSBS) && (im->width & 1)) return false;
+  const uint8_t *ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
+  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  for (int k = 0; k < O_COUNT; ++k)
+    if ((p->outputs & bits[k]) && !ptrs[k]) return false;
+  if ((p->outputs & ~DIBR_OUT_DEPTH) && o->pitch < 3 * static_cast<int64_t>(im->width)) return false;
+  if ((p->outputs & DIBR_OUT_DEPTH) && o->depth_pitch < im->width) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const dibr_params *p,
+                                                    int n_params, const dibr_outputs *outs, void *cuda_stream) {
+  if (n < 1 || n > kStaticMaxImages || !imgs || !p || !outs || (n_params != 1 && n_params != n))
+    return DIBR_E_INVALID;
+  int64_t rows = 0;
+  int nch_max = 1, srow = 128;
+  for (int i = 0; i < n; ++i) {
+    if (!valid_image(&p[n_params == 1 ? 0 : i], &imgs[i], &outs[i])) return DIBR_E_INVALID;
+    rows += imgs[i].height;
+    const int nch = (imgs[i].width + kChunk - 1) / kChunk;
+    nch_max = nch_max > nch ? nch_max : nch;
+    const int need = 3 * imgs[i].width > 48 * nch ? 3 * imgs[i].width : 48 * nch;
+    srow = srow > round_up(need, 128) ? srow : round_up(need, 128);
+  }
+  // work units of at least 32 rows, more when the unit list would not fit
+  int rows_per_unit = 32;
+  auto count_units = [&](int r) {
+    int64_t u = 0;
+    for (int i = 0; i < n; ++i) u += (imgs[i].height + r - 1) / r;
+    return u;
+  };
+  while (count_units(rows_per_unit) > kStaticMaxUnits) rows_per_unit *= 2;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
+    cudaGetLastError();
+    return DIBR_E_CUDA;
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  std::lock_guard<std::mutex> lk(g_mu);
+  dibr_status s = setup_device(dev);
+  if (s != DIBR_OK) return s;
+  const DeviceSetup &d = g_dev[dev];
+
+  // launch plan for the widest image (the same rule as the context's batched launch)
+  const int nc = round_up(nch_max, 32);
+  const int max_per = (65536 / (nc * 128)) < (2048 / nc) ? (65536 / (nc * 128)) : (2048 / nc);
+  int best = 0, nb = 4;
+  for (int k = 4; k <= kMaxRing; ++k) {
+    const int tot = band_smem_layout(k, srow, nch_max, DS_BINOM5).total;
+    if (tot > d.max_smem) continue;
+    int per = d.smem_per_sm / (tot + 1024);
+    per = per < max_per ? per : max_per;
+    if (per > best || (per == best && per > 0)) {
+      best = per;
+      nb = k;
+    }
+  }
+  if (best < 1) return DIBR_E_INVALID;
+  const int smem = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
+
+  // descriptors and units into the host staging; the header zeroes the counter and the
+  // status word, which every launch needs to start at zero
+  std::memset(g_staging, 0, kDescOff);
+  ImageDesc *descs = reinterpret_cast<ImageDesc *>(g_staging + kDescOff);
+  int4 *units = reinterpret_cast<int4 *>(g_staging + kUnitsOff);
+  int n_units = 0;
+  for (int i = 0; i < n; ++i) {
+    const dibr_image &im = imgs[i];
+    const dibr_params &pp = p[n_params == 1 ? 0 : i];
+    const dibr_outputs &o = outs[i];
+    ImageDesc &dd = descs[i];
+    std::memset(&dd, 0, sizeof(dd));
+    dd.in = im.rgb;
+    dd.in_pitch = im.pitch;
+    dd.out[O_ANA] = o.anaglyph;
+    dd.out[O_LEFT] = o.left;
+    dd.out[O_RIGHT] = o.right;
+    dd.out[O_HSBS] = o.hsbs;
+    dd.out[O_DEPTH] = o.depth;
+    dd.out_pitch = o.pitch;
+    dd.depth_pitch = o.depth_pitch;
+    dd.W = im.width;
+    dd.H = im.height;
+    dd.nch = (im.width + kChunk - 1) / kChunk;
+    dd.row_bytes = 3 * im.width;
+    dd.outputs = pp.outputs;
+    dd.warp_mode = pp.warp_mode;
+    dd.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
+    shift_tables(&pp, dd.lut_h, dd.lut_n);
+    for (int y0 = 0; y0 < im.height; y0 += rows_per_unit)
+      units[n_units++] = make_int4(i, y0, y0 + rows_per_unit < im.height ? y0 + rows_per_unit : im.height, 0);
+  }
+  // From pageable memory the copy has left g_staging when the call returns.
+  const size_t bytes = kUnitsOff + sizeof(int4) * static_cast<size_t>(n_units);
+  cudaError_t e = cudaMemcpyAsync(d.scratch, g_staging, bytes, cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return DIBR_E_CUDA;
+  BatchArgs b;
+  b.descs = reinterpret_cast<const ImageDesc *>(d.scratch + kDescOff);
+  b.units = reinterpret_cast<const int4 *>(d.scratch + kUnitsOff);
+  b.n_units = n_units;
+  b.counter = reinterpret_cast<int *>(d.scratch);
+  b.status = reinterpret_cast<int *>(d.scratch) + 1;
+  b.timeout_ns = 2000000000ull;
+  b.nb = nb;
+  b.srow = srow;
+  b.nch_max = nch_max;
+  b.nc = nc;
+  const int grid = n_units < d.sms * best ? n_units : d.sms * best;
+  e = launch_batch(b, grid, smem, stream);
+  if (e != cudaSuccess) return DIBR_E_CUDA;
+  // blocking: wait for the batch, then read the device status word
+  int status = 0;
+  e = cudaMemcpyAsync(&status, b.status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return DIBR_E_CUDA;
+  return status ? DIBR_E_TIMEOUT : DIBR_OK;
+}

@@ -27,7 +27,7 @@ SYMBOLS = ("dibr_params_default", "dibr_validate", "dibr_shift_tables", "dibr_cr
            "dibr_destroy", "dibr_last_error", "dibr_stream", "dibr_synthesize_image",
            "dibr_enqueue_image", "dibr_synchronize", "dibr_synthesize_batch", "dibr_enqueue_batch",
            "dibr_open_stream", "dibr_submit_frame", "dibr_poll", "dibr_close_stream",
-           "dibr_set_tuning", "dibr_get_tuning")
+           "dibr_set_tuning", "dibr_get_tuning", "dibr_synthesize_batch_static")
 
 
 class dibr_params(C.Structure):
@@ -113,6 +113,8 @@ def load(build_if_missing=True):
         "dibr_close_stream": (C.c_int, [ctx, C.c_int]),
         "dibr_set_tuning": (C.c_int, [ctx, P(dibr_tuning)]),
         "dibr_get_tuning": (C.c_int, [ctx, P(dibr_tuning)]),
+        "dibr_synthesize_batch_static": (C.c_int, [C.c_int, P(dibr_image), P(dibr_params), C.c_int,
+                                                   P(dibr_outputs), C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -198,6 +200,10 @@ def dibr_set_tuning(ctx, t):
 
 def dibr_get_tuning(ctx, t):
     return _fn("dibr_get_tuning")(ctx, C.byref(t))
+
+
+def dibr_synthesize_batch_static(n, imgs, p, n_params, outs, stream):
+    return _fn("dibr_synthesize_batch_static")(n, imgs, p, n_params, outs, stream)
 
 
 # ------------------------------------------------------------------ convenience layer
