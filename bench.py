@@ -26,6 +26,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -40,6 +42,48 @@ CONFIG = {"workload": "4K UHD still: 3840x2160 RGB uint8, 40 objects, P=64, bino
           "width": W4K, "height": H4K, "max_parallax_px": P4K,
           "outputs": list(OUTPUTS), "depth_rule": "binom5", "disparity_rule": "paper",
           "warp_mode": "forward"}
+
+
+def reduce_max(x, dist=None, device="cpu"):
+    """Maximum of a float over all ranks (the value itself when running alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, seconds_per_rank, world, dist=None, device="cpu"):
+    """Units processed by all ranks / the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / reduce_max(seconds_per_rank, dist, device)
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("dibr_band.cu", "dibr_internal.h", "dibr_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2009_09501_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per launch of the band kernel from the committed ncu summary, or None
+    when the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "band_kernel_4k_stereo.md")
+    try:
+        vals = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ":" in line:
+                    k, v = line[2:].split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("kernel_source_digest") != kernel_source_digest():
+            return None, "stale (kernel changed since the capture)"
+        return float(vals["dram_bytes_per_launch"]), "ncu capture, profiles/band_kernel_4k_stereo.md"
+    except Exception:
+        return None, "no capture"
 
 
 def load_peaks():
@@ -185,6 +229,117 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def bench_batch(D, torch, ctx, stream, n=64):
+    """Batched workload: n images drawn from the 720p..8K classes (P = 2.5 % of the width,
+    anaglyph), one persistent launch vs one launch per image, frames/s on the device."""
+    from paper_2009_09501_gb300 import scenes
+    sizes = scenes.batch_sizes(n)
+    pool = {wh: torch.from_numpy(scenes.Scene(wh[0], wh[1], 2009_09501 + 4 + i, 40, "gauss8").frame(0)).cuda()
+            for i, wh in enumerate(scenes.BATCH_CLASSES)}
+    ins = [pool[wh] for wh in sizes]
+    outs = [{"anaglyph": torch.empty_like(t)} for t in ins]
+    prms = [D.make_params(max_parallax=scenes.batch_parallax(t.shape[1]), outputs=("anaglyph",)) for t in ins]
+    pixels = sum(t.shape[0] * t.shape[1] for t in ins)
+
+    def timed(fn, reps=5):
+        fn()
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        ctx.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0
+
+    t_batch = timed(lambda: ctx.enqueue_batch(ins, prms, outs))
+    t_single = timed(lambda: [ctx.enqueue_image(i, q, o) for i, q, o in zip(ins, prms, outs)])
+    return {"images": n, "megapixels": pixels / 1e6, "frames_per_s_batched": n / t_batch,
+            "frames_per_s_per_image_launches": n / t_single, "speedup": t_single / t_batch,
+            "gb_per_s_batched": pixels * 6 / t_batch / 1e9, "sizes": "seeded mix of %s" % list(scenes.BATCH_CLASSES)}
+
+
+def bench_video(D, torch, ctx, frames=300):
+    """4K video streamed from pinned host memory through one serving stream (H2D, kernel
+    and D2H overlapped across frames), anaglyph, P = 64."""
+    from paper_2009_09501_gb300 import scenes
+    sc = scenes.Scene(3840, 2160, 2009_09501 + 3, 40, "gauss8", moving=True)
+    pool = [torch.from_numpy(sc.frame(k)).pin_memory() for k in range(2)]
+    outs = [torch.empty((2160, 3840, 3), dtype=torch.uint8).pin_memory() for _ in range(4)]
+    p = D.make_params(max_parallax=P4K, outputs=("anaglyph",))
+    with D.Context(device=torch.cuda.current_device()) as c:
+        sid = c.open_stream(3840, 2160, p)
+        lat, done, k = [], 0, 0
+        t0 = time.perf_counter()
+        while done < frames:
+            while k < frames and k - done < 4:
+                st = c.submit_frame(sid, k, pool[k % 2].numpy(), {"anaglyph": outs[k % 4].numpy()})
+                if st != D.DIBR_OK:
+                    break
+                k += 1
+            for comp in c.poll(16, 100000):
+                assert comp.status == D.DIBR_OK
+                lat.append((comp.t_done_ns - comp.t_submit_ns) / 1e6)
+                done += 1
+        el = time.perf_counter() - t0
+        c.close_stream(sid)
+    fb = 3840 * 2160 * 3
+    return {"frames": frames, "frames_per_s": frames / el, "host_link_gb_per_s": 2 * fb * frames / el / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+
+
+def bench_served(D, torch, seconds):
+    """Serving: 4 x 1080p and 4 x 4K streams, Poisson arrivals at 30 fps per stream,
+    anaglyph, P = 2.5 % of the width; per-frame latency submit -> outputs in host memory."""
+    from paper_2009_09501_gb300 import scenes
+    sizes = [(1920, 1080)] * 4 + [(3840, 2160)] * 4
+    rng = np.random.default_rng(2009_09501 + 5)
+    frames = [torch.from_numpy(scenes.stream_scene(k, W, H).frame(0)).pin_memory() for k, (W, H) in enumerate(sizes)]
+    with D.Context(device=torch.cuda.current_device()) as c:
+        sids = [c.open_stream(W, H, D.make_params(max_parallax=scenes.batch_parallax(W), outputs=("anaglyph",)))
+                for (W, H) in sizes]
+        outs = [[torch.empty_like(f).pin_memory() for _ in range(20)] for f in frames]
+        events = []
+        for k in range(len(sizes)):
+            t = 0.0
+            while True:
+                t += rng.exponential(1.0 / 30.0)
+                if t >= seconds:
+                    break
+                events.append((t, k))
+        events.sort()
+        lat = {k: [] for k in range(len(sizes))}
+        refused, n_sub, seq = 0, 0, [0] * len(sizes)
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(events) or sum(len(v) for v in lat.values()) < n_sub:
+            now = time.perf_counter() - t0
+            while i < len(events) and events[i][0] <= now:
+                k = events[i][1]
+                o = outs[k][seq[k] % 20]
+                st = c.submit_frame(sids[k], seq[k], frames[k].numpy(), {"anaglyph": o.numpy()})
+                if st == D.DIBR_OK:
+                    n_sub += 1
+                else:
+                    refused += 1
+                seq[k] += 1
+                i += 1
+            for comp in c.poll(64, 500):
+                k = sids.index(comp.stream_id)
+                lat[k].append((comp.t_done_ns - comp.t_submit_ns) / 1e6)
+            if now > seconds + 30:
+                break
+        el = time.perf_counter() - t0
+        for s_ in sids:
+            c.close_stream(s_)
+    all_l = [x for v in lat.values() for x in v]
+    l4k = [x for k in range(4, 8) for x in lat[k]]
+    return {"streams": "4 x 1920x1080 + 4 x 3840x2160 @ 30 fps Poisson", "seconds": seconds,
+            "frames": len(all_l), "frames_per_s": len(all_l) / el, "refused": refused,
+            "p50_ms": float(np.percentile(all_l, 50)), "p99_ms": float(np.percentile(all_l, 99)),
+            "p99_ms_4k": float(np.percentile(l4k, 99)) if l4k else None}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -260,11 +415,8 @@ def run_ours(args):
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     launch_ms = [a.elapsed_time(b) for a, b in ev]
     mean_launch_ms = float(np.mean(launch_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1000.0)
+    value = whole_job_rate(K, total_ms / 1000.0, world, dist, "cuda")
+    total_ms = reduce_max(total_ms, dist, "cuda")
 
     # end to end through the public API with pinned host buffers
     host_in = torch.from_numpy(img).pin_memory()
@@ -280,14 +432,16 @@ def run_ours(args):
     for _ in range(n_e2e):
         ctx.check(sync_fn(h, D.C.byref(hi), pref, D.C.byref(ho)))
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * n_e2e / e2e_s
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_value = world * n_e2e / float(t.item())
+    e2e_value = whole_job_rate(n_e2e, e2e_s, world, dist, "cuda")
 
+    extra = {}
+    if world == 1 and not args.quick:
+        extra["batch"] = bench_batch(D, torch, ctx, stream)
+        extra["video"] = bench_video(D, torch, ctx)
+        extra["served"] = bench_served(D, torch, args.served_seconds)
     if rank == 0:
         peak, peak_kind = load_peaks()
+        traffic, traffic_src = load_traffic()
         achieved = ALG_BYTES / (mean_launch_ms / 1000.0) / 1e9
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -296,7 +450,7 @@ def run_ours(args):
             "config": dict(CONFIG, l2_defeat="rotating %d buffer sets of %.1f MB (> 2x L2 of %.0f MB)"
                            % (nsets, set_bytes / 1e6, l2 / 1e6), parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": args.traffic,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                          "kernel": "band_kernel", "alg_bytes_per_launch": ALG_BYTES,
                          "mean_launch_us": mean_launch_ms * 1000.0,
@@ -307,6 +461,7 @@ def run_ours(args):
             "gpu_launches": K,
             "clocks": sampler.summary(t_host0 - 0.02, t_host1 + 0.02),
         }
+        out.update(extra)
         if world == 1 and not args.no_cpu_baseline:
             v, cores, n, el = oracle_frames_per_s(img)
             v1, n1, el1 = oracle_single_core(img)
@@ -328,8 +483,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the fused kernel, if captured")
+    ap.add_argument("--quick", action="store_true", help="skip the batch, video and served sections")
+    ap.add_argument("--served-seconds", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
