@@ -387,3 +387,37 @@ def test_xbf_brute_force_tiny(oracle):
             v = num / den
             if abs(v - math.floor(v) - 0.5) > 1e-9:
                 assert got[y, x] == math.floor(v + 0.5), (y, x)
+
+
+
+def test_fill_comes_from_the_farther_side_of_a_depth_edge(oracle):
+    # one depth edge per row (two flat regions): every hole that has filled targets on
+    # both sides shows the colour of a source from the farther (smaller depth) region --
+    # the background-side reading of the fill, which the directional rule implements
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(300):
+        W = int(rng.integers(8, 80))
+        e = int(rng.integers(1, W))
+        d1, d2 = (int(v) for v in rng.integers(0, 256, 2))
+        if d1 == d2:
+            continue
+        D = np.array([[d1] * e + [d2] * (W - e)], np.uint8)
+        img = np.zeros((1, W, 3), np.uint8)
+        img[0, :, 0] = np.arange(W)  # colour encodes the source column
+        P, rule = int(rng.integers(1, 96)), int(rng.integers(0, 2))
+        out = oracle.from_depth(img, D, oracle.params(max_parallax=P, disparity_rule=rule), want=("left", "right"))
+        hL, hR = oracle.disparity_lut(rule, P, 150)
+        for view, h in (("left", hL), ("right", hR)):
+            covered = np.zeros(W, bool)
+            for x in range(W):
+                t = x - int(h[D[0, x]])
+                if 0 <= t < W:
+                    covered[t] = True
+            idx = np.flatnonzero(covered)
+            for t in np.flatnonzero(~covered):
+                if idx.size and idx[0] < t < idx[-1]:
+                    src = int(out[view][0, t, 0])
+                    assert D[0, src] == min(d1, d2), (view, W, e, d1, d2, P, rule, t)
+                    checked += 1
+    assert checked > 100
