@@ -209,16 +209,21 @@ __device__ __noinline__ int warp_walk_right(const uint32_t *zb, int t, int W, in
 }
 
 // Entries shown by the 16 targets of this thread in one view: the z-buffer winner, or
-// for a hole the winner of the nearest filled target on the background (smaller
-// depth) side -- the left one on a tie -- or of the only side; with no filled target in
-// the row, the input pixel at the hole itself (row-local inpainting).
+// for a hole the winner of the nearest filled target on its farther side -- of the
+// nearest filled targets to its left and right, the one whose winner has the smaller
+// depth (the left one on a tie, the only one at a row edge); the input pixel at the hole
+// when the row has no filled target.
 //
-// Neighbours outside the thread's 16 targets come from the nearest lower / higher lane
-// that has a filled target (ballot + shuffle) or, past the warp's 512 targets, from a
-// warp-wide search of the z-buffer.
-__device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0,
-                                             int npx, int W, int lane, int warp_lo, int warp_hi,
-                                             uint32_t (&k)[16]) {
+// Two register sweeps: left to right carrying the last filled key into the holes, then
+// right to left carrying the last filled key and keeping it where it is strictly
+// farther.  Entries are (255 - depth) << 24 | colour, so "c strictly farther than k" is
+// the unsigned compare c > (k | 0xFFFFFF).  The keys carried into the chunk come from
+// the nearest lane on each side with a filled target (ballot + shuffle) or, past the
+// warp's 512 targets, from a warp-wide search of the z-buffer.  A missing right key
+// carries in as 0, which is never strictly farther; holes with no left key (row starts)
+// are set afterwards on a path of their own.
+__device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0, int npx, int W,
+                                             int lane, int warp_lo, int warp_hi, uint32_t (&k)[16]) {
   const uint32_t zs = smem_addr(zb);
   if (npx > 0) {
 #pragma unroll
@@ -239,50 +244,51 @@ __device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *
   const uint32_t holes = ~m & rowmask;
   if (!__any_sync(0xffffffffu, holes != 0u)) return;
 
-  // filled targets nearest to this lane's chunk on either side
+  const int first = m ? x0 + __ffs(m) - 1 : kNoTarget;  // this chunk's first / last filled target
   const int last = m ? x0 + 31 - __clz(m) : -1;
-  const int first = m ? x0 + __ffs(m) - 1 : kNoTarget;
+  // holes before the chunk's first filled target need the key carried in from the left,
+  // holes after its last one the key carried in from the right
+  const uint32_t before = m ? holes & ((1u << (first - x0)) - 1u) : holes;
+  const uint32_t after = m ? holes & ~((2u << (last - x0)) - 1u) : holes;
   const uint32_t lanes = __ballot_sync(0xffffffffu, m != 0u);
   const uint32_t lower = lanes & ((1u << lane) - 1u);
   const uint32_t upper = lanes & ~((2u << lane) - 1u);
-  int prev = __shfl_sync(0xffffffffu, last, lower ? 31 - __clz(lower) : lane);
-  int next = __shfl_sync(0xffffffffu, first, upper ? __ffs(upper) - 1 : lane);
-  if (!lower) prev = -1;
-  if (!upper) next = kNoTarget;
-  if (__any_sync(0xffffffffu, holes && prev < 0)) {
-    const int wl = warp_lo > 0 ? warp_walk_left(zb, warp_lo - 1, lane) : -1;
-    if (prev < 0) prev = wl;
+  int nl = __shfl_sync(0xffffffffu, last, lower ? 31 - __clz(lower) : lane);
+  int nr = __shfl_sync(0xffffffffu, first, upper ? __ffs(upper) - 1 : lane);
+  if (!lower) nl = -1;
+  if (!upper) nr = kNoTarget;
+  if (__any_sync(0xffffffffu, before && !lower)) {
+    const int w = warp_lo > 0 ? warp_walk_left(zb, warp_lo - 1, lane) : -1;
+    if (!lower) nl = w;
   }
-  if (__any_sync(0xffffffffu, holes && next == kNoTarget)) {
-    const int wr = warp_hi < W ? warp_walk_right(zb, warp_hi, W, lane) : kNoTarget;
-    if (next == kNoTarget) next = wr;
+  if (__any_sync(0xffffffffu, after && !upper)) {
+    const int w = warp_hi < W ? warp_walk_right(zb, warp_hi, W, lane) : kNoTarget;
+    if (!upper) nr = w;
   }
-  // one pass per run of holes: its two neighbours and the farther of them fill it
-  uint32_t rest = holes;
-  while (rest) {
-    const int i0 = __ffs(rest) - 1;
-    const int len = __ffs(~(rest >> i0)) - 1;
-    const uint32_t run = ((1u << len) - 1u) << i0;
-    const uint32_t below = m & ((1u << i0) - 1u);
-    const uint32_t above = m & ~((1u << (i0 + len)) - 1u);
-    const int l = below ? x0 + 31 - __clz(below) : prev;
-    const int r = above ? x0 + __ffs(above) - 1 : next;
-    const uint32_t kl = l >= 0 ? lds_u32(zs + 4u * l) : kEmpty;
-    const uint32_t kr = r < W ? lds_u32(zs + 4u * r) : kEmpty;
-    uint32_t s = kEmpty;
-    if (kl != kEmpty && kr != kEmpty) s = (kl >> 24) >= (kr >> 24) ? kl : kr;  // smaller depth
-    else if (kl != kEmpty) s = kl;
-    else if (kr != kEmpty) s = kr;
-    if (s != kEmpty) {
+  // left to right: every hole takes the last filled key (entries past the row's end take
+  // whatever they take: they are never stored and this sweep carries nothing leftwards)
+  uint32_t c = nl >= 0 ? lds_u32(zs + 4u * nl) : kEmpty;
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if ((run >> j) & 1u) k[j] = s;
-    } else {  // no filled target anywhere in the row: the input pixel stays
+  for (int j = 0; j < 16; ++j) {
+    if (k[j] != kEmpty) c = k[j];
+    k[j] = c;
+  }
+  // right to left: a hole keeps the right key where it is strictly farther
+  c = nr < W ? lds_u32(zs + 4u * nr) : 0u;
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if ((run >> j) & 1u) k[j] = rgb_at(rgbrow, x0 + j);
-    }
-    rest &= ~run;
+  for (int j = 15; j >= 0; --j) {
+    if ((m >> j) & 1u) c = k[j];
+    else if (c > (k[j] | 0xFFFFFFu)) k[j] = c;
+  }
+  // holes before the first filled target of the row: the right key, or the input pixel
+  // when the row has no filled target
+  const bool row_start = nl < 0 && before != 0u;
+  if (__any_sync(0xffffffffu, row_start) && row_start) {
+    const int r = m ? first : nr;
+    const uint32_t cr = r < W ? lds_u32(zs + 4u * r) : kEmpty;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      if ((before >> j) & 1u) k[j] = cr != kEmpty ? cr : rgb_at(rgbrow, x0 + j);
   }
 }
 
@@ -555,17 +561,39 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       const uint32_t ls = smem_addr(m.lut4);
       const uint32_t zls = smem_addr(zl), zrs = smem_addr(zr);
       const bool full_warp = warp_hi - warp_lo == 32 * kChunk;
+      if (full_warp) {
+        // four steps at a time: all their shared loads are issued before their atomics
+#pragma unroll
+        for (int g = 0; g < kChunk / 4; ++g) {
+          uint32_t dv[4], cw[8];
+          lds_u8_step32x4(ds + 128 * g, dv);
+          lds_u32_pair_step96x4(cws + 384 * g, cw);
+          int4 lh[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) lh[j] = lds_s32x4(ls + 16 * dv[j]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int x = xb + 32 * (4 * g + j);
+            const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh[j].z);
+            const int tl = x + lh[j].x, tr = x + lh[j].y;
+            if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
+            if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+          }
+        }
+      } else {
+        // the row's last, partial warp: columns from warp_hi on do not exist
 #pragma unroll 4
-      for (int i = 0; i < kChunk; ++i) {
-        const int x = xb + 32 * i;
-        if (full_warp || x < warp_hi) {
-          const uint32_t dv = lds_u8(ds + 32 * i);
-          const int4 lh = lds_s32x4(ls + 16 * dv);
-          const uint32_t w0 = lds_u32(cws + 96 * i), w1 = lds_u32(cws + 96 * i + 4);
-          const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh.z);
-          const int tl = x + lh.x, tr = x + lh.y;
-          if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
-          if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+        for (int i = 0; i < kChunk; ++i) {
+          const int x = xb + 32 * i;
+          if (x < warp_hi) {
+            const uint32_t dv = lds_u8(ds + 32 * i);
+            const int4 lh = lds_s32x4(ls + 16 * dv);
+            const uint32_t w0 = lds_u32(cws + 96 * i), w1 = lds_u32(cws + 96 * i + 4);
+            const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh.z);
+            const int tl = x + lh.x, tr = x + lh.y;
+            if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
+            if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+          }
         }
       }
     }
@@ -714,6 +742,12 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     __syncthreads();
     if (!run_band(j, m, un.y, un.z, kbase, b.status, b.timeout_ns)) break;
   }
+  // No unit is left for this CTA: the next launch of the batch (another group of images,
+  // independent of this one) may start filling the SMs this launch leaves.  A chained
+  // launch's CTAs then wait for the previous launch to complete before they exit, so that
+  // the work after the batch in stream order still follows all of it.
+  griddep_launch_dependents();
+  griddep_wait();
 }
 
 template <typename K>
@@ -737,12 +771,22 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, cudaStream_t st) {
+cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {
   static bool done = false;
   cudaError_t e = allow_smem(batch_kernel, done);
   if (e != cudaSuccess) return e;
-  batch_kernel<<<grid, b.nc, smem_bytes, st>>>(b);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(b.nc);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = chained ? 1 : 0;
+  e = cudaLaunchKernelEx(&cfg, batch_kernel, b);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace dibr

@@ -96,42 +96,26 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
       dof += static_cast<size_t>(dp) * im.height;
     }
   }
-  // --- shared-memory plan for the widest image
-  int nch_max = 1, srow = 128;
+  // --- one launch per group of images of equal block width, widest first
+  std::vector<int> widths(n), heights(n), class_of(n), order(n);
   for (int i = 0; i < n; ++i) {
-    const int nch = (imgs[i].width + kChunk - 1) / kChunk;
-    nch_max = std::max(nch_max, nch);
-    srow = std::max(srow, round_up(std::max(row_bytes[i], 48 * nch), 128));
+    widths[i] = imgs[i].width;
+    heights[i] = imgs[i].height;
   }
-  const int nc = round_up(nch_max, 32);
-  const int max_per = std::max(1, std::min(65536 / (nc * 128), 2048 / nc));
-  auto per_for = [&](int nb) {
-    const int tot = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
-    if (tot > max_smem) return 0;
-    int per = std::min(max_per, smem_per_sm / (tot + 1024));
-    if (tuning.ctas_per_sm > 0) per = std::min(per, tuning.ctas_per_sm);
-    return per;
-  };
-  const int max_nb = tuning.ring_slots > 0 ? std::max(4, std::min(kMaxRing, tuning.ring_slots)) : kMaxRing;
-  int best = 0, nb = 4;
-  for (int k = 4; k <= max_nb; ++k) best = std::max(best, per_for(k));
-  if (best < 1) {
+  BatchClass cls[kMaxClasses];
+  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm};
+  const int nclass = plan_batch_classes(n, widths.data(), row_bytes.data(), lim, class_of.data(), cls);
+  if (nclass < 1) {
     set_error("batch images too wide for shared memory");
     return DIBR_E_INVALID;
   }
-  for (int k = 4; k <= max_nb; ++k)
-    if (per_for(k) == best) nb = k;
-  const int smem = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
+  order_by_area(n, widths.data(), heights.data(), order.data());
 
-  // --- descriptors and units (largest images first), staged in pinned memory
-  std::vector<int> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return static_cast<int64_t>(imgs[a].width) * imgs[a].height > static_cast<int64_t>(imgs[b].width) * imgs[b].height;
-  });
+  // --- descriptors and units, staged in pinned memory; each group's units are
+  // contiguous, largest images first
   int n_units = 0;
   for (int i = 0; i < n; ++i) n_units += (imgs[i].height + rows_per_unit - 1) / rows_per_unit;
-  // [counter][pad] [descs] [units]: every part 256-byte aligned (the kernel reads the
+  // [counters][pad] [descs] [units]: every part 256-byte aligned (the kernel reads the
   // units as int4 and the descriptors' 64-bit fields)
   const size_t off_desc = 256;
   const size_t off_units = (off_desc + sizeof(ImageDesc) * n + 255) / 256 * 256;
@@ -151,12 +135,10 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
   if (!batch_copy_done && cudaEventCreateWithFlags(&batch_copy_done, cudaEventDisableTiming) != cudaSuccess)
     return DIBR_E_CUDA;
   if ((s = ensure(batch_desc, total)) != DIBR_OK) return s;
-  std::memset(batch_pinned, 0, off_desc);
+  std::memset(batch_pinned, 0, off_desc);  // the groups' unit counters start at zero
   ImageDesc *descs = reinterpret_cast<ImageDesc *>(batch_pinned + off_desc);
   int4 *units = reinterpret_cast<int4 *>(batch_pinned + off_units);
-  int u = 0;
-  for (int oi = 0; oi < n; ++oi) {
-    const int i = order[oi];
+  for (int i = 0; i < n; ++i) {
     const dibr_image &im = imgs[i];
     const dibr_params &pp = p[n_params == 1 ? 0 : i];
     const dibr_outputs &o = outs[i];
@@ -175,32 +157,44 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
     d.depth_pitch = o.depth_pitch;
     d.W = im.width;
     d.H = im.height;
-    d.nch = (im.width + kChunk - 1) / kChunk;
+    d.nch = chunks_of(im.width);
     d.row_bytes = row_bytes[i];
     d.outputs = pp.outputs;
     d.warp_mode = pp.warp_mode;
     d.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : pp.depth_rule == DIBR_DEPTH_LUMA ? DS_LUMA : DS_GLOBAL;
     shift_tables(&pp, d.lut_h, d.lut_n);
-    for (int y0 = 0; y0 < im.height; y0 += rows_per_unit) units[u++] = make_int4(i, y0, std::min(im.height, y0 + rows_per_unit), 0);
+  }
+  int u = 0;
+  for (int c = 0; c < nclass; ++c) {
+    cls[c].unit_begin = u;
+    for (int oi = 0; oi < n; ++oi) {
+      const int i = order[oi];
+      if (class_of[i] != c) continue;
+      for (int y0 = 0; y0 < imgs[i].height; y0 += rows_per_unit)
+        units[u++] = make_int4(i, y0, std::min(imgs[i].height, y0 + rows_per_unit), 0);
+    }
+    cls[c].n_units = u - cls[c].unit_begin;
   }
   cudaError_t e = cudaMemcpyAsync(batch_desc.ptr, batch_pinned, total, cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(batch_copy_done, stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
-  BatchArgs b;
-  b.descs = reinterpret_cast<const ImageDesc *>(batch_desc.ptr + off_desc);
-  b.units = reinterpret_cast<const int4 *>(batch_desc.ptr + off_units);
-  b.n_units = n_units;
-  b.counter = reinterpret_cast<int *>(batch_desc.ptr);
-  b.status = status_dev;
-  b.timeout_ns = timeout_ns;
-  b.nb = nb;
-  b.srow = srow;
-  b.nch_max = nch_max;
-  b.nc = nc;
-  const int grid = std::max(1, std::min(n_units, num_sms * best));
-  e = launch_batch(b, grid, smem, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
-  ++launches;
+  for (int c = 0; c < nclass; ++c) {
+    BatchArgs b;
+    b.descs = reinterpret_cast<const ImageDesc *>(batch_desc.ptr + off_desc);
+    b.units = reinterpret_cast<const int4 *>(batch_desc.ptr + off_units) + cls[c].unit_begin;
+    b.n_units = cls[c].n_units;
+    b.counter = reinterpret_cast<int *>(batch_desc.ptr) + c;
+    b.status = status_dev;
+    b.timeout_ns = timeout_ns;
+    b.nb = cls[c].nb;
+    b.srow = cls[c].srow;
+    b.nch_max = cls[c].nch_max;
+    b.nc = cls[c].nc;
+    const int grid = std::max(1, std::min(cls[c].n_units, num_sms * cls[c].per));
+    e = launch_batch(b, grid, cls[c].smem, c > 0, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    ++launches;
+  }
   return DIBR_OK;
 }
 

@@ -111,7 +111,7 @@ struct alignas(16) ImageDesc {
 
 static_assert(sizeof(ImageDesc) % 16 == 0, "descriptors are read as an array");
 
-// Arguments of the batched kernel: descriptors, work units {image, first row, end row,
+// Arguments of one batched launch: descriptors, work units {image, first row, end row,
 // 0} in the order they are handed out, and the counter the CTAs take units from.
 struct BatchArgs {
   const ImageDesc *descs;
@@ -123,9 +123,100 @@ struct BatchArgs {
   int32_t nb, srow, nch_max, nc;
 };
 
+// ---- planning a batch (host; no allocation, so the no-allocation entry point shares it)
+//
+// A block of the band kernel is as wide as its widest row needs (one thread per 16
+// columns, whole warps).  A batch mixing 720p and 8K frames in one launch would run every
+// 720p row on an 8K-wide block, most of it idle, at the 8K block's one CTA per SM.  So the
+// images are grouped by block width and each group gets a launch of its own plan; the
+// launches follow one another on the stream, widest first, each allowed to start while
+// the previous one finishes its last units (programmatic dependent launch).
+constexpr int kMaxClasses = 16;  // distinct block widths: 32 .. 480 threads in steps of 32
+
+struct BatchClass {
+  int nc;          // threads per block
+  int nch_max;     // 16-column chunks of the widest row in the group
+  int srow;        // bytes per ring slot
+  int nb, per;     // ring slots; CTAs per SM
+  int smem;        // dynamic shared memory per block
+  int unit_begin, n_units;
+};
+
+struct BatchLimits {
+  int max_smem, smem_per_sm;  // device limits
+  int ring_slots, ctas_per_sm;  // tuning caps (0: none)
+};
+
+inline int chunks_of(int width) { return (width + kChunk - 1) / kChunk; }
+inline int block_of(int width) { return round_up(chunks_of(width), 32); }
+
+// Groups the n images by block width (widest first), plans each group's ring and CTAs per
+// SM, and sets class_of[i].  Returns the number of groups, or -1 if some group fits no plan.
+inline int plan_batch_classes(int n, const int *width, const int *row_bytes, const BatchLimits &lim,
+                              int *class_of, BatchClass *cls) {
+  int nclass = 0;
+  for (int i = 0; i < n; ++i) {
+    const int nc = block_of(width[i]);
+    int c = 0;
+    while (c < nclass && cls[c].nc > nc) ++c;
+    if (c == nclass || cls[c].nc != nc) {
+      if (nclass == kMaxClasses) return -1;
+      for (int k = nclass; k > c; --k) cls[k] = cls[k - 1];
+      cls[c] = BatchClass{nc, 1, 128, 4, 0, 0, 0, 0};
+      ++nclass;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    int c = 0;
+    while (cls[c].nc != block_of(width[i])) ++c;
+    class_of[i] = c;
+    const int nch = chunks_of(width[i]);
+    const int need = row_bytes[i] > 48 * nch ? row_bytes[i] : 48 * nch;
+    if (nch > cls[c].nch_max) cls[c].nch_max = nch;
+    if (round_up(need, 128) > cls[c].srow) cls[c].srow = round_up(need, 128);
+  }
+  const int max_nb = lim.ring_slots > 0 ? (lim.ring_slots < 4 ? 4 : lim.ring_slots < kMaxRing ? lim.ring_slots : kMaxRing)
+                                        : kMaxRing;
+  for (int c = 0; c < nclass; ++c) {
+    BatchClass &k = cls[c];
+    const int by_regs = 65536 / (k.nc * 128), by_threads = 2048 / k.nc;
+    const int max_per = by_regs < by_threads ? by_regs : by_threads;
+    k.per = 0;
+    for (int nb = 4; nb <= max_nb; ++nb) {
+      const int tot = band_smem_layout(nb, k.srow, k.nch_max, DS_BINOM5).total;
+      if (tot > lim.max_smem) continue;
+      int per = lim.smem_per_sm / (tot + 1024);
+      if (per > max_per) per = max_per;
+      if (lim.ctas_per_sm > 0 && per > lim.ctas_per_sm) per = lim.ctas_per_sm;
+      if (per >= 1 && per >= k.per) {  // the deepest ring at the best CTAs per SM
+        k.per = per;
+        k.nb = nb;
+      }
+    }
+    if (k.per < 1) return -1;
+    k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, DS_BINOM5).total;
+  }
+  return nclass;
+}
+
+// order[0..n) = image indices, largest area first (stable insertion sort, no allocation)
+inline void order_by_area(int n, const int *width, const int *height, int *order) {
+  for (int i = 0; i < n; ++i) {
+    const int64_t a = static_cast<int64_t>(width[i]) * height[i];
+    int k = i;
+    while (k > 0 && static_cast<int64_t>(width[order[k - 1]]) * height[order[k - 1]] < a) {
+      order[k] = order[k - 1];
+      --k;
+    }
+    order[k] = i;
+  }
+}
+
 // Host launchers (dibr_band.cu, dibr_xbf.cu).
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st);
-cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, cudaStream_t st);
+// chained: may start while the previous launch on the stream finishes (the previous
+// launch is a batch launch of the same call).
+cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st);
 int band_max_threads(int ctas_per_sm);
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,

@@ -144,9 +144,39 @@ __device__ __forceinline__ uint4 lds_u32x4(uint32_t a) {
   return v;
 }
 // atomic minimum without a returned value
+// Bytes at a, a+32, a+64, a+96: one lane's depths for four consecutive 32-column steps.
+__device__ __forceinline__ void lds_u8_step32x4(uint32_t a, uint32_t (&v)[4]) {
+  asm volatile(
+      "ld.shared.u8 %0, [%4];\n\t"
+      "ld.shared.u8 %1, [%4+32];\n\t"
+      "ld.shared.u8 %2, [%4+64];\n\t"
+      "ld.shared.u8 %3, [%4+96];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+      : "r"(a));
+}
+// Word pairs at a + 96 i and a + 96 i + 4, i = 0..3: one lane's colour bytes (3 per
+// column) for four consecutive 32-column steps.
+__device__ __forceinline__ void lds_u32_pair_step96x4(uint32_t a, uint32_t (&v)[8]) {
+  asm volatile(
+      "ld.shared.u32 %0, [%8];\n\t"
+      "ld.shared.u32 %1, [%8+4];\n\t"
+      "ld.shared.u32 %2, [%8+96];\n\t"
+      "ld.shared.u32 %3, [%8+100];\n\t"
+      "ld.shared.u32 %4, [%8+192];\n\t"
+      "ld.shared.u32 %5, [%8+196];\n\t"
+      "ld.shared.u32 %6, [%8+288];\n\t"
+      "ld.shared.u32 %7, [%8+292];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(a));
+}
 __device__ __forceinline__ void reds_min(uint32_t a, uint32_t v) {
   asm volatile("red.shared.min.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
+
+// Programmatic dependent launch: let the next launch on the stream start / wait for the
+// previous one (with its memory) to complete; both are no-ops for a launch without it.
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Named barrier 1 over the consumer threads only.
 __device__ __forceinline__ void consumer_sync(int nthreads) {

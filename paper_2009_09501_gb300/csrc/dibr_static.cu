@@ -25,7 +25,8 @@ namespace {
 constexpr int kStaticMaxImages = 64;
 constexpr int kStaticMaxUnits = 8192;
 constexpr int kStaticMaxDevices = 64;
-constexpr size_t kDescOff = 256;  // [counter][status] ... [descriptors] [units]
+constexpr size_t kDescOff = 256;  // [group counters][status] ... [descriptors] [units]
+constexpr int kStatusWord = kMaxClasses;  // int index of the status word in the header
 constexpr size_t kUnitsOff = (kDescOff + sizeof(ImageDesc) * kStaticMaxImages + 255) / 256 * 256;
 constexpr size_t kStaticBytes = kUnitsOff + sizeof(int4) * kStaticMaxUnits;  // 267,008 bytes
 
@@ -100,15 +101,12 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
                                                     int n_params, const dibr_outputs *outs, void *cuda_stream) {
   if (n < 1 || n > kStaticMaxImages || !imgs || !p || !outs || (n_params != 1 && n_params != n))
     return DIBR_E_INVALID;
-  int64_t rows = 0;
-  int nch_max = 1, srow = 128;
+  int widths[kStaticMaxImages], heights[kStaticMaxImages], row_bytes[kStaticMaxImages];
   for (int i = 0; i < n; ++i) {
     if (!valid_image(&p[n_params == 1 ? 0 : i], &imgs[i], &outs[i])) return DIBR_E_INVALID;
-    rows += imgs[i].height;
-    const int nch = (imgs[i].width + kChunk - 1) / kChunk;
-    nch_max = nch_max > nch ? nch_max : nch;
-    const int need = 3 * imgs[i].width > 48 * nch ? 3 * imgs[i].width : 48 * nch;
-    srow = srow > round_up(need, 128) ? srow : round_up(need, 128);
+    widths[i] = imgs[i].width;
+    heights[i] = imgs[i].height;
+    row_bytes[i] = 3 * imgs[i].width;
   }
   // work units of at least 32 rows, more when the unit list would not fit
   int rows_per_unit = 32;
@@ -130,29 +128,19 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
   if (s != DIBR_OK) return s;
   const DeviceSetup &d = g_dev[dev];
 
-  // launch plan for the widest image (the same rule as the context's batched launch)
-  const int nc = round_up(nch_max, 32);
-  const int max_per = (65536 / (nc * 128)) < (2048 / nc) ? (65536 / (nc * 128)) : (2048 / nc);
-  int best = 0, nb = 4;
-  for (int k = 4; k <= kMaxRing; ++k) {
-    const int tot = band_smem_layout(k, srow, nch_max, DS_BINOM5).total;
-    if (tot > d.max_smem) continue;
-    int per = d.smem_per_sm / (tot + 1024);
-    per = per < max_per ? per : max_per;
-    if (per > best || (per == best && per > 0)) {
-      best = per;
-      nb = k;
-    }
-  }
-  if (best < 1) return DIBR_E_INVALID;
-  const int smem = band_smem_layout(nb, srow, nch_max, DS_BINOM5).total;
+  // one launch per group of equal block width (the context's batched launch plan)
+  BatchClass cls[kMaxClasses];
+  int class_of[kStaticMaxImages], order[kStaticMaxImages];
+  const BatchLimits lim{d.max_smem, d.smem_per_sm, 0, 0};
+  const int nclass = plan_batch_classes(n, widths, row_bytes, lim, class_of, cls);
+  if (nclass < 1) return DIBR_E_INVALID;
+  order_by_area(n, widths, heights, order);
 
-  // descriptors and units into the host staging; the header zeroes the counter and the
-  // status word, which every launch needs to start at zero
+  // descriptors and units into the host staging; the header zeroes the groups' unit
+  // counters and the status word, which every call needs to start at zero
   std::memset(g_staging, 0, kDescOff);
   ImageDesc *descs = reinterpret_cast<ImageDesc *>(g_staging + kDescOff);
   int4 *units = reinterpret_cast<int4 *>(g_staging + kUnitsOff);
-  int n_units = 0;
   for (int i = 0; i < n; ++i) {
     const dibr_image &im = imgs[i];
     const dibr_params &pp = p[n_params == 1 ? 0 : i];
@@ -170,36 +158,48 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     dd.depth_pitch = o.depth_pitch;
     dd.W = im.width;
     dd.H = im.height;
-    dd.nch = (im.width + kChunk - 1) / kChunk;
+    dd.nch = chunks_of(im.width);
     dd.row_bytes = 3 * im.width;
     dd.outputs = pp.outputs;
     dd.warp_mode = pp.warp_mode;
     dd.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
     shift_tables(&pp, dd.lut_h, dd.lut_n);
-    for (int y0 = 0; y0 < im.height; y0 += rows_per_unit)
-      units[n_units++] = make_int4(i, y0, y0 + rows_per_unit < im.height ? y0 + rows_per_unit : im.height, 0);
+  }
+  int n_units = 0;
+  for (int c = 0; c < nclass; ++c) {
+    cls[c].unit_begin = n_units;
+    for (int oi = 0; oi < n; ++oi) {
+      const int i = order[oi];
+      if (class_of[i] != c) continue;
+      for (int y0 = 0; y0 < imgs[i].height; y0 += rows_per_unit)
+        units[n_units++] = make_int4(i, y0, y0 + rows_per_unit < imgs[i].height ? y0 + rows_per_unit : imgs[i].height, 0);
+    }
+    cls[c].n_units = n_units - cls[c].unit_begin;
   }
   // From pageable memory the copy has left g_staging when the call returns.
   const size_t bytes = kUnitsOff + sizeof(int4) * static_cast<size_t>(n_units);
   cudaError_t e = cudaMemcpyAsync(d.scratch, g_staging, bytes, cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return DIBR_E_CUDA;
-  BatchArgs b;
-  b.descs = reinterpret_cast<const ImageDesc *>(d.scratch + kDescOff);
-  b.units = reinterpret_cast<const int4 *>(d.scratch + kUnitsOff);
-  b.n_units = n_units;
-  b.counter = reinterpret_cast<int *>(d.scratch);
-  b.status = reinterpret_cast<int *>(d.scratch) + 1;
-  b.timeout_ns = 2000000000ull;
-  b.nb = nb;
-  b.srow = srow;
-  b.nch_max = nch_max;
-  b.nc = nc;
-  const int grid = n_units < d.sms * best ? n_units : d.sms * best;
-  e = launch_batch(b, grid, smem, stream);
-  if (e != cudaSuccess) return DIBR_E_CUDA;
+  int *status_dev = reinterpret_cast<int *>(d.scratch) + kStatusWord;
+  for (int c = 0; c < nclass; ++c) {
+    BatchArgs b;
+    b.descs = reinterpret_cast<const ImageDesc *>(d.scratch + kDescOff);
+    b.units = reinterpret_cast<const int4 *>(d.scratch + kUnitsOff) + cls[c].unit_begin;
+    b.n_units = cls[c].n_units;
+    b.counter = reinterpret_cast<int *>(d.scratch) + c;
+    b.status = status_dev;
+    b.timeout_ns = 2000000000ull;
+    b.nb = cls[c].nb;
+    b.srow = cls[c].srow;
+    b.nch_max = cls[c].nch_max;
+    b.nc = cls[c].nc;
+    const int grid = cls[c].n_units < d.sms * cls[c].per ? cls[c].n_units : d.sms * cls[c].per;
+    e = launch_batch(b, grid > 0 ? grid : 1, cls[c].smem, c > 0, stream);
+    if (e != cudaSuccess) return DIBR_E_CUDA;
+  }
   // blocking: wait for the batch, then read the device status word
   int status = 0;
-  e = cudaMemcpyAsync(&status, b.status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  e = cudaMemcpyAsync(&status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return DIBR_E_CUDA;
   return status ? DIBR_E_TIMEOUT : DIBR_OK;
