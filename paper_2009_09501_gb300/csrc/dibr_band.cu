@@ -400,6 +400,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   const int nload = lb - la;
   const int zimg = a.nch * kChunk;  // this image's targets, rounded up to whole chunks
   const uint32_t k0 = kbase;
+  // g / nb as umulhi(g, ceil(2^32 / nb)): exact while g * (nb - 1) < 2^32, far beyond the
+  // loads one CTA makes in a launch
+  const uint32_t ring_rcp = 0xFFFFFFFFu / static_cast<uint32_t>(nb) + 1u;
+  auto ring_div = [&](uint32_t g) { return __umulhi(g, ring_rcp); };
 
   // Row k = r - la of the band is the (k0 + k)-th load of this CTA: slot (k0+k) % nb.
   // Warp 0 issues the loads of rows [issued, upto); the caller guarantees every
@@ -412,7 +416,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       if (tid == 0 && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
       for (int k = issued; k < upto; ++k) {
         const uint32_t g = k0 + k;
-        const int s = g % nb;
+        const int s = static_cast<int>(g - ring_div(g) * nb);
         uint8_t *dst = m.ring + s * m.srow;
         if (a.load_mode == LM_BULK) {
           if (tid == 0) {
@@ -456,10 +460,13 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   const int warp_lo = (tid & ~31) * kChunk;
   const int warp_hi = min(W, warp_lo + 32 * kChunk);
   bool timed_out = false;
-  auto slot = [&](int r) { return m.ring + ((k0 + (r - la)) % nb) * m.srow; };
-  auto wait_row = [&](int r) {
+  auto slot = [&](int r) {
     const uint32_t g = k0 + (r - la);
-    if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, timeout_ns)) timed_out = true;
+    return m.ring + (g - ring_div(g) * nb) * m.srow;
+  };
+  auto wait_row = [&](int r) {
+    const uint32_t g = k0 + (r - la), q = ring_div(g);
+    if (!mbar_wait_bounded(&m.full[g - q * nb], q & 1, timeout_ns)) timed_out = true;
   };
 
   const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
