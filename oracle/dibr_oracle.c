@@ -40,7 +40,9 @@
 enum { OR_DEPTH_LUMA = 0, OR_DEPTH_BINOM5 = 1, OR_DEPTH_XBF = 2 };
 enum { OR_DISP_PAPER = 0, OR_DISP_LINEAR = 1 };
 enum { OR_WARP_FORWARD = 0, OR_WARP_GATHER_FIG3 = 1 };
-enum { OR_FILL_ROW = 0, OR_FILL_NONE = 1 };
+/* Hole fill: the row-local copy alone, or followed by the iterative 2-D block inpainting
+ * of Fig. 3 (inpaint2d_oracle.c) over the holes of each view. */
+enum { OR_FILL_ROW = 0, OR_FILL_INPAINT2D = 1 };
 
 typedef struct {
     int32_t depth_rule;      /* OR_DEPTH_* */
@@ -51,7 +53,12 @@ typedef struct {
     double  xbf_sigma_s;     /* spatial sigma of the cross-bilateral filter, pixels */
     double  xbf_sigma_r;     /* range sigma, RGB units */
     int32_t xbf_radius;      /* half width of the square window */
+    int32_t fill_mode;       /* OR_FILL_* */
+    int32_t inpaint_block;   /* side of the square blocks of the 2-D inpainting */
 } or_params;
+
+int64_t or_inpaint2d(const uint8_t *view, int W, int H, int64_t pitch, const uint8_t *damaged,
+                     int64_t dpitch, int bw, int bh, uint8_t *out, int64_t out_pitch);
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -225,28 +232,60 @@ static void gather_row(const uint8_t *Drow, int W, int P, int T, int is_left, in
  * Figs. 4-5): red-cyan anaglyph (red from the left view, green and blue from the right
  * view, Fig. 3), full left and right views, anamorphic half side-by-side (each view
  * squeezed 2:1 horizontally by pairwise means rounded half up; left view in the left
- * half), and the filtered depth map itself.  Any pointer may be NULL. */
+ * half), the filtered depth map itself and the holes of the forward warp (one byte per
+ * pixel: bit 0 a hole of the left view, bit 1 of the right view).  Any pointer may be
+ * NULL. */
 typedef struct {
-    uint8_t *anaglyph, *left, *right, *hsbs, *depth;
+    uint8_t *anaglyph, *left, *right, *hsbs, *depth, *holes;
     int64_t pitch;        /* bytes between rows of the RGB outputs */
-    int64_t depth_pitch;  /* bytes between rows of the depth output */
+    int64_t depth_pitch;  /* bytes between rows of the one-byte maps (depth, holes) */
 } or_outputs;
 
+/* One row of the formatted outputs from one row of each view. */
+static void compose_row(const uint8_t *Lrow, const uint8_t *Rrow, int W, int y, const or_outputs *out)
+{
+    if (out->left) memcpy(out->left + (int64_t)y * out->pitch, Lrow, 3 * (size_t)W);
+    if (out->right) memcpy(out->right + (int64_t)y * out->pitch, Rrow, 3 * (size_t)W);
+    if (out->anaglyph) {
+        uint8_t *a = out->anaglyph + (int64_t)y * out->pitch;
+        for (int t = 0; t < W; ++t) {
+            a[3 * t + 0] = Lrow[3 * t + 0];
+            a[3 * t + 1] = Rrow[3 * t + 1];
+            a[3 * t + 2] = Rrow[3 * t + 2];
+        }
+    }
+    if (out->hsbs) {
+        uint8_t *s = out->hsbs + (int64_t)y * out->pitch;
+        int half = W / 2;
+        for (int x = 0; x < W; ++x) {
+            const uint8_t *v = x < half ? Lrow : Rrow;
+            int k = x < half ? x : x - half;
+            for (int c = 0; c < 3; ++c)
+                s[3 * x + c] = (uint8_t)((v[3 * (2 * k) + c] + v[3 * (2 * k + 1) + c] + 1) >> 1);
+        }
+    }
+}
+
 /* The back half of the pipeline (warp, occlusion, fill, formatting) for a given depth
- * map D (W x H, tightly packed).  Returns 0, or -1 for invalid arguments. */
+ * map D (W x H, tightly packed).  Returns 0, or -1 for invalid arguments.  The frame is
+ * reconstructed whole first (both views and their holes), then -- with the 2-D fill
+ * mode -- each view is inpainted, then the outputs are formatted. */
 int or_from_depth(const uint8_t *rgb, int W, int H, int64_t pitch, const uint8_t *D,
                   const or_params *prm, const or_outputs *out)
 {
     if (W < 1 || H < 1 || pitch < 3 * (int64_t)W) return -1;
     if (out->hsbs && (W & 1)) return -1;
+    if (prm->fill_mode != OR_FILL_ROW && prm->fill_mode != OR_FILL_INPAINT2D) return -1;
+    if (prm->fill_mode == OR_FILL_INPAINT2D && prm->inpaint_block < 1) return -1;
     int16_t hL[256], hR[256];
     or_disparity_lut(prm->disparity_rule, prm->max_parallax, prm->threshold, hL, hR);
+    const size_t npx = (size_t)W * (size_t)H;
     int32_t *wx = (int32_t *)malloc(sizeof(int32_t) * (size_t)W);
     int32_t *wd = (int32_t *)malloc(sizeof(int32_t) * (size_t)W);
     int32_t *sL = (int32_t *)malloc(sizeof(int32_t) * (size_t)W);
     int32_t *sR = (int32_t *)malloc(sizeof(int32_t) * (size_t)W);
-    uint8_t *Lrow = (uint8_t *)malloc(3 * (size_t)W);
-    uint8_t *Rrow = (uint8_t *)malloc(3 * (size_t)W);
+    uint8_t *Lv = (uint8_t *)malloc(3 * npx), *Rv = (uint8_t *)malloc(3 * npx);
+    uint8_t *holeL = (uint8_t *)calloc(npx, 1), *holeR = (uint8_t *)calloc(npx, 1);
     for (int y = 0; y < H; ++y) {
         const uint8_t *Drow = D + (int64_t)y * W;
         const uint8_t *Irow = rgb + (int64_t)y * pitch;
@@ -255,36 +294,34 @@ int or_from_depth(const uint8_t *rgb, int W, int H, int64_t pitch, const uint8_t
             gather_row(Drow, W, prm->max_parallax, prm->threshold, 0, sR);
         } else {
             warp_fill_row(Drow, W, hL, 1, wx, wd, sL);
+            for (int t = 0; t < W; ++t) holeL[(size_t)y * W + t] = wx[t] < 0;
             warp_fill_row(Drow, W, hR, 0, wx, wd, sR);
+            for (int t = 0; t < W; ++t) holeR[(size_t)y * W + t] = wx[t] < 0;
         }
         for (int t = 0; t < W; ++t)
             for (int c = 0; c < 3; ++c) {
-                Lrow[3 * t + c] = Irow[3 * sL[t] + c];
-                Rrow[3 * t + c] = Irow[3 * sR[t] + c];
+                Lv[3 * ((size_t)y * W + t) + c] = Irow[3 * sL[t] + c];
+                Rv[3 * ((size_t)y * W + t) + c] = Irow[3 * sR[t] + c];
             }
-        if (out->left) memcpy(out->left + (int64_t)y * out->pitch, Lrow, 3 * (size_t)W);
-        if (out->right) memcpy(out->right + (int64_t)y * out->pitch, Rrow, 3 * (size_t)W);
-        if (out->anaglyph) {
-            uint8_t *a = out->anaglyph + (int64_t)y * out->pitch;
-            for (int t = 0; t < W; ++t) {
-                a[3 * t + 0] = Lrow[3 * t + 0];
-                a[3 * t + 1] = Rrow[3 * t + 1];
-                a[3 * t + 2] = Rrow[3 * t + 2];
-            }
-        }
-        if (out->hsbs) {
-            uint8_t *s = out->hsbs + (int64_t)y * out->pitch;
-            int half = W / 2;
-            for (int x = 0; x < W; ++x) {
-                const uint8_t *v = x < half ? Lrow : Rrow;
-                int k = x < half ? x : x - half;
-                for (int c = 0; c < 3; ++c)
-                    s[3 * x + c] = (uint8_t)((v[3 * (2 * k) + c] + v[3 * (2 * k + 1) + c] + 1) >> 1);
-            }
-        }
-        if (out->depth) memcpy(out->depth + (int64_t)y * out->depth_pitch, Drow, (size_t)W);
     }
-    free(wx); free(wd); free(sL); free(sR); free(Lrow); free(Rrow);
+    if (prm->fill_mode == OR_FILL_INPAINT2D) {
+        uint8_t *tmp = (uint8_t *)malloc(3 * npx);
+        const int b = prm->inpaint_block;
+        or_inpaint2d(Lv, W, H, 3 * (int64_t)W, holeL, W, b, b, tmp, 3 * (int64_t)W);
+        memcpy(Lv, tmp, 3 * npx);
+        or_inpaint2d(Rv, W, H, 3 * (int64_t)W, holeR, W, b, b, tmp, 3 * (int64_t)W);
+        memcpy(Rv, tmp, 3 * npx);
+        free(tmp);
+    }
+    for (int y = 0; y < H; ++y) {
+        compose_row(Lv + 3 * (size_t)y * W, Rv + 3 * (size_t)y * W, W, y, out);
+        if (out->depth) memcpy(out->depth + (int64_t)y * out->depth_pitch, D + (int64_t)y * W, (size_t)W);
+        if (out->holes)
+            for (int t = 0; t < W; ++t)
+                out->holes[(int64_t)y * out->depth_pitch + t] =
+                    (uint8_t)(holeL[(size_t)y * W + t] | (holeR[(size_t)y * W + t] << 1));
+    }
+    free(wx); free(wd); free(sL); free(sR); free(Lv); free(Rv); free(holeL); free(holeR);
     return 0;
 }
 
@@ -322,6 +359,7 @@ int or_dibr_rows(const uint8_t *rgb, int W, int H, int64_t pitch, const or_param
                  const or_outputs *out, int y0, int y1)
 {
     if (y0 < 0 || y1 > H || y0 >= y1) return -1;
+    if (prm->fill_mode != OR_FILL_ROW) return -1; /* the 2-D fill is not row-local */
     int ctx = prm->depth_rule == OR_DEPTH_XBF ? prm->xbf_radius : 2;
     int a = y0 - ctx < 0 ? 0 : y0 - ctx;
     int b = y1 + ctx > H ? H : y1 + ctx;
@@ -339,6 +377,7 @@ int or_dibr_rows(const uint8_t *rgb, int W, int H, int64_t pitch, const or_param
         if (o.right) o.right += off;
         if (o.hsbs) o.hsbs += off;
         if (o.depth) o.depth += doff;
+        if (o.holes) o.holes += doff;
         rc = or_from_depth(rgb + (int64_t)y0 * pitch, W, y1 - y0, pitch,
                            D + (int64_t)(y0 - a) * W, prm, &o);
     }

@@ -6,7 +6,9 @@ the two cross-check each other on tiny images:
   * the depth filter as one direct 5 x 5 sum instead of two separable passes;
   * occlusion by listing every source that lands on a target and taking the best one,
     instead of a running z-buffer;
-  * hole fill by listing all filled targets to each side, instead of walking.
+  * hole fill by listing all filled targets to each side, instead of walking;
+  * the 2-D inpainting on a dictionary of the damaged pixels and a full copy of the frame
+    per block, instead of a bordered block matrix.
 Sections of the paper followed: Sec. 3 (six components), Sec. 4 (stage list), Fig. 3
 (shift rule, threshold, out-of-range fallback, red-cyan channel map).
 """
@@ -138,3 +140,41 @@ def pipeline(img, P, T=150, rule="paper", depth="binom5", mode="forward", D=None
             hsbs.append(row)
         out["hsbs"] = hsbs
     return out
+
+
+def inpaint2d(view, damaged, block):
+    """Fig. 3's iterative block inpainting: per block a private copy of the whole frame;
+    damaged pixels listed block-column by block-column; passes over the list repair every
+    damaged pixel with >= 2 undamaged 8-neighbours (mean rounded half up, visible at once
+    to later pixels of the pass) until none is left or a pass repairs nothing."""
+    H, W = len(view), len(view[0])
+    out = [[list(map(int, view[y][x])) for x in range(W)] for y in range(H)]
+    left = 0
+    for by in range(0, H, block):
+        for bx in range(0, W, block):
+            frame = [[list(map(int, view[y][x])) for x in range(W)] for y in range(H)]
+            dmg = {(x, y): bool(damaged[y][x]) for y in range(H) for x in range(W)}
+            order = [(x, y) for x in range(bx, min(bx + block, W)) for y in range(by, min(by + block, H))
+                     if dmg[(x, y)]]
+            todo = len(order)
+            while todo:
+                fixed = 0
+                for (x, y) in order:
+                    if not dmg[(x, y)]:
+                        continue
+                    good = [(x + dx, y + dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                            if (dx or dy) and 0 <= x + dx < W and 0 <= y + dy < H and not dmg[(x + dx, y + dy)]]
+                    if len(good) < 2:
+                        continue
+                    dmg[(x, y)] = False
+                    todo -= 1
+                    fixed += 1
+                    frame[y][x] = [math.floor(Fraction(sum(frame[v][u][c] for (u, v) in good), len(good)) + HALF)
+                                   for c in range(3)]
+                if not fixed:
+                    break
+            left += todo
+            for y in range(by, min(by + block, H)):
+                for x in range(bx, min(bx + block, W)):
+                    out[y][x] = frame[y][x]
+    return out, left

@@ -13,20 +13,23 @@ from . import build as _build
 DEPTH_LUMA, DEPTH_BINOM5, DEPTH_XBF = 0, 1, 2
 DISP_PAPER, DISP_LINEAR = 0, 1
 WARP_FORWARD, WARP_GATHER_FIG3 = 0, 1
+FILL_ROW, FILL_INPAINT2D = 0, 1
 
-OUTPUT_NAMES = ("anaglyph", "left", "right", "hsbs", "depth")
+OUTPUT_NAMES = ("anaglyph", "left", "right", "hsbs", "depth", "holes")
 
 
 class _Params(C.Structure):
     _fields_ = [("depth_rule", C.c_int32), ("disparity_rule", C.c_int32),
                 ("warp_mode", C.c_int32), ("max_parallax", C.c_int32),
                 ("threshold", C.c_int32), ("xbf_sigma_s", C.c_double),
-                ("xbf_sigma_r", C.c_double), ("xbf_radius", C.c_int32)]
+                ("xbf_sigma_r", C.c_double), ("xbf_radius", C.c_int32),
+                ("fill_mode", C.c_int32), ("inpaint_block", C.c_int32)]
 
 
 class _Outputs(C.Structure):
     _fields_ = [("anaglyph", C.c_void_p), ("left", C.c_void_p), ("right", C.c_void_p),
-                ("hsbs", C.c_void_p), ("depth", C.c_void_p), ("pitch", C.c_int64),
+                ("hsbs", C.c_void_p), ("depth", C.c_void_p), ("holes", C.c_void_p),
+                ("pitch", C.c_int64),
                 ("depth_pitch", C.c_int64)]
 
 
@@ -55,25 +58,27 @@ def lib():
         L.or_dibr_rows.argtypes = [u8p, C.c_int, C.c_int, C.c_int64, C.POINTER(_Params),
                                    C.POINTER(_Outputs), C.c_int, C.c_int]
         L.or_dibr_rows.restype = C.c_int
-        if hasattr(L, "or_inpaint2d"):
-            L.or_inpaint2d.argtypes = [u8p, C.c_int, C.c_int, C.c_int64, u8p, C.c_int64,
-                                       C.c_int, C.c_int, C.c_int, u8p, C.c_int64]
-            L.or_inpaint2d.restype = C.c_int
+        L.or_inpaint2d.argtypes = [u8p, C.c_int, C.c_int, C.c_int64, u8p, C.c_int64,
+                                   C.c_int, C.c_int, u8p, C.c_int64]
+        L.or_inpaint2d.restype = C.c_int64
         _lib = L
     return _lib
 
 
 def params(depth_rule=DEPTH_BINOM5, disparity_rule=DISP_PAPER, warp_mode=WARP_FORWARD,
-           max_parallax=16, threshold=150, xbf_sigma_s=1.5, xbf_sigma_r=16.0, xbf_radius=2):
+           max_parallax=16, threshold=150, xbf_sigma_s=1.5, xbf_sigma_r=16.0, xbf_radius=2,
+           fill_mode=FILL_ROW, inpaint_block=32):
     """Oracle parameter record; defaults follow Fig. 3 (T = 150) and the default smoothing."""
     return dict(depth_rule=depth_rule, disparity_rule=disparity_rule, warp_mode=warp_mode,
                 max_parallax=max_parallax, threshold=threshold, xbf_sigma_s=xbf_sigma_s,
-                xbf_sigma_r=xbf_sigma_r, xbf_radius=xbf_radius)
+                xbf_sigma_r=xbf_sigma_r, xbf_radius=xbf_radius, fill_mode=fill_mode,
+                inpaint_block=inpaint_block)
 
 
 def _cparams(p):
     return _Params(p["depth_rule"], p["disparity_rule"], p["warp_mode"], p["max_parallax"],
-                   p["threshold"], p["xbf_sigma_s"], p["xbf_sigma_r"], p["xbf_radius"])
+                   p["threshold"], p["xbf_sigma_s"], p["xbf_sigma_r"], p["xbf_radius"],
+                   p.get("fill_mode", FILL_ROW), p.get("inpaint_block", 32))
 
 
 def _ptr(a):
@@ -121,7 +126,7 @@ def disparity_lut(rule, P, T=150):
 def _alloc_outputs(H, W, want):
     outs = {}
     for name in want:
-        if name == "depth":
+        if name in ("depth", "holes"):
             outs[name] = np.zeros((H, W), np.uint8)
         else:
             outs[name] = np.zeros((H, W, 3), np.uint8)
@@ -176,3 +181,18 @@ def dibr_rows(img, p, y0, y1, want=("anaglyph", "left", "right")):
     if rc != 0:
         raise ValueError("oracle rejected the arguments")
     return outs
+
+
+def inpaint2d(view, damaged, block=32, block_h=None):
+    """The iterative 2-D block inpainting (Fig. 3) of one view; returns (result, pixels
+    left damaged)."""
+    view = _check_img(view)
+    H, W, _ = view.shape
+    dmg = np.ascontiguousarray(damaged != 0, dtype=np.uint8)
+    assert dmg.shape == (H, W)
+    out = np.empty_like(view)
+    left = lib().or_inpaint2d(_ptr(view), W, H, 3 * W, _ptr(dmg), W, block,
+                              block if block_h is None else block_h, _ptr(out), 3 * W)
+    if left < 0:
+        raise ValueError("oracle rejected the arguments")
+    return out, int(left)
