@@ -259,6 +259,35 @@ def bench_batch(D, torch, ctx, stream, n=64):
             "gb_per_s_batched": pixels * 6 / t_batch / 1e9, "sizes": "seeded mix of %s" % list(scenes.BATCH_CLASSES)}
 
 
+def bench_inpaint(D, torch, ctx, stream, reps=200):
+    """4K L + R + anaglyph, P = 64, with the 2-D block inpainting fill (Fig. 3, 32 x 32
+    blocks) against the row fill on the same rotating buffer sets (more than 2x L2)."""
+    from paper_2009_09501_gb300 import scenes
+    img = torch.from_numpy(scenes.config_scene(2)).cuda()
+    H, W = img.shape[:2]
+    sets = []
+    for _ in range(4):
+        i = img.clone()
+        sets.append((i, {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS}))
+    res = {}
+    for name, fill in (("row_fill", D.DIBR_FILL_ROW), ("inpaint2d", D.DIBR_FILL_INPAINT2D)):
+        p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, hole_fill=fill, inpaint_block=32)
+        for k in range(10):
+            ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        e1.record(stream)
+        ctx.synchronize()
+        res[name] = e0.elapsed_time(e1) / reps * 1000.0
+    return {"workload": "3840x2160, P=64, L+R+anaglyph, 2-D block inpainting (32x32 blocks) after the row fill",
+            "frames_per_s": 1e6 / res["inpaint2d"], "us_per_frame": res["inpaint2d"],
+            "row_fill_us_per_frame": res["row_fill"], "inpaint_overhead_us": res["inpaint2d"] - res["row_fill"],
+            "launches_per_frame": 2}
+
+
 def bench_video(D, torch, ctx, frames=300):
     """4K video streamed from pinned host memory through one serving stream (H2D, kernel
     and D2H overlapped across frames), anaglyph, P = 64."""
@@ -437,6 +466,7 @@ def run_ours(args):
     extra = {}
     if world == 1 and not args.quick:
         extra["batch"] = bench_batch(D, torch, ctx, stream)
+        extra["inpaint2d"] = bench_inpaint(D, torch, ctx, stream)
         extra["video"] = bench_video(D, torch, ctx)
         extra["served"] = bench_served(D, torch, args.served_seconds)
     if rank == 0:

@@ -83,9 +83,27 @@ enum { DIBR_WARP_FORWARD = 0, DIBR_WARP_GATHER_FIG3 = 1 };
  * LEFT/RIGHT: the two full-resolution views.
  * HSBS: anamorphic half side-by-side; each view squeezed 2:1 by pairwise channel means
  *   rounded half up, left view in the left half (requires an even width).
- * DEPTH: the filtered depth map (one byte per pixel). */
+ * DEPTH: the filtered depth map (one byte per pixel).
+ * HOLES: the holes of the forward warp, one byte per pixel: bit 0 set where no source
+ *   reached the target in the left view, bit 1 the same for the right view (zero
+ *   everywhere with DIBR_WARP_GATHER_FIG3). */
 enum { DIBR_OUT_ANAGLYPH = 1, DIBR_OUT_LEFT = 2, DIBR_OUT_RIGHT = 4, DIBR_OUT_HSBS = 8,
-       DIBR_OUT_DEPTH = 16 };
+       DIBR_OUT_DEPTH = 16, DIBR_OUT_HOLES = 32 };
+
+/* Hole fill (Sec. 3: post-processed left / right frames; Fig. 3, left column: the
+ * iterative inpainting algorithm).
+ * DIBR_FILL_ROW: the row-local copy described under DIBR_WARP_FORWARD.
+ * DIBR_FILL_INPAINT2D: the row-local copy, then Fig. 3's iterative block inpainting over
+ *   the holes of each view: the frame is cut into inpaint_block x inpaint_block blocks;
+ *   in each block the holes are visited block column by block column, and a hole with at
+ *   least two non-hole 8-neighbours takes the mean of their colours (per channel, rounded
+ *   half up) and stops being a hole at once for the holes after it; the visits repeat
+ *   while one of them repairs something.  A block sees pixels outside it as the row-local
+ *   copy left them.  Holes never repaired keep the row-local colour.  Anaglyph and HSBS
+ *   are formatted from the inpainted views.  Single-image calls only
+ *   (dibr_synthesize_image / dibr_enqueue_image); with DIBR_OUT_HSBS the block side must
+ *   be even. */
+enum { DIBR_FILL_ROW = 0, DIBR_FILL_INPAINT2D = 1 };
 
 typedef struct {
     int32_t depth_rule;       /* DIBR_DEPTH_* */
@@ -97,6 +115,8 @@ typedef struct {
     float   xbf_sigma_r;      /* > 0, RGB units (default 16) */
     int32_t xbf_radius;       /* 1..8 (default 2) */
     uint32_t outputs;         /* OR of DIBR_OUT_*; at least one */
+    int32_t hole_fill;        /* DIBR_FILL_* (default DIBR_FILL_ROW) */
+    int32_t inpaint_block;    /* DIBR_FILL_INPAINT2D block side, 1..32 (default 32) */
 } dibr_params;
 
 /* One input frame.  on_device != 0: rgb is a device pointer of the context's device;
@@ -110,10 +130,10 @@ typedef struct {
 
 /* Where the outputs go.  Pointers for outputs not requested in dibr_params.outputs are
  * ignored and may be NULL; requested ones must be non-NULL.  RGB outputs are width x
- * height x 3 with row pitch `pitch` (>= 3*width); the depth output is width x height with
- * row pitch `depth_pitch` (>= width).  on_device as in dibr_image. */
+ * height x 3 with row pitch `pitch` (>= 3*width); the depth and holes outputs are width x
+ * height with row pitch `depth_pitch` (>= width).  on_device as in dibr_image. */
 typedef struct {
-    uint8_t *anaglyph, *left, *right, *hsbs, *depth;
+    uint8_t *anaglyph, *left, *right, *hsbs, *depth, *holes;
     int64_t pitch;
     int64_t depth_pitch;
     int32_t on_device;

@@ -87,8 +87,15 @@ static dibr_status check_params(const dibr_params *p, const dibr_image *img, std
       return DIBR_E_INVALID;
     }
   }
-  const uint32_t all = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS | DIBR_OUT_DEPTH;
-  if (p->outputs == 0 || (p->outputs & ~all)) { *why = "outputs must be a non-empty set of DIBR_OUT_* bits"; return DIBR_E_INVALID; }
+  if (p->outputs == 0 || (p->outputs & ~kAllOutputs)) { *why = "outputs must be a non-empty set of DIBR_OUT_* bits"; return DIBR_E_INVALID; }
+  if (!valid_enum(p->hole_fill, 0, 1)) { *why = "unknown hole_fill"; return DIBR_E_INVALID; }
+  if (p->hole_fill == DIBR_FILL_INPAINT2D) {
+    if (p->inpaint_block < 1 || p->inpaint_block > 32) { *why = "inpaint_block outside 1..32"; return DIBR_E_INVALID; }
+    if ((p->outputs & DIBR_OUT_HSBS) && (p->inpaint_block & 1)) {
+      *why = "the 2-D fill with HSBS needs an even inpaint_block";
+      return DIBR_E_INVALID;
+    }
+  }
   if (img) {
     if (img->width < 1 || img->height < 1 || img->width > kMaxWidth || img->height > 65535) {
       *why = "image size outside 1..7680 x 1..65535";
@@ -104,15 +111,14 @@ static dibr_status check_params(const dibr_params *p, const dibr_image *img, std
 static dibr_status check_outputs(const dibr_params *p, const dibr_image *img, const dibr_outputs *o,
                                  std::string *why) {
   if (!o) { *why = "outputs is NULL"; return DIBR_E_INVALID; }
-  const uint8_t *ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
-  bool rgb_out = false;
+  bool rgb_out = false, map_out = false;
   for (int i = 0; i < O_COUNT; ++i) {
-    if ((p->outputs & bits[i]) && !ptrs[i]) { *why = "a requested output pointer is NULL"; return DIBR_E_INVALID; }
-    if ((p->outputs & bits[i]) && i != O_DEPTH) rgb_out = true;
+    if (!(p->outputs & kOutBits[i])) continue;
+    if (!out_slot(*o, i)) { *why = "a requested output pointer is NULL"; return DIBR_E_INVALID; }
+    (is_map_output(i) ? map_out : rgb_out) = true;
   }
   if (rgb_out && o->pitch < 3 * static_cast<int64_t>(img->width)) { *why = "output pitch < 3*width"; return DIBR_E_INVALID; }
-  if ((p->outputs & DIBR_OUT_DEPTH) && o->depth_pitch < img->width) { *why = "depth_pitch < width"; return DIBR_E_INVALID; }
+  if (map_out && o->depth_pitch < img->width) { *why = "depth_pitch < width"; return DIBR_E_INVALID; }
   return DIBR_OK;
 }
 
@@ -326,19 +332,61 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     a.depth_in = nullptr;
     a.depth_in_pitch = 0;
   }
-  a.out[O_ANA] = o->anaglyph;
-  a.out[O_LEFT] = o->left;
-  a.out[O_RIGHT] = o->right;
-  a.out[O_HSBS] = o->hsbs;
-  a.out[O_DEPTH] = o->depth;
+  for (int i = 0; i < O_COUNT; ++i) a.out[i] = out_slot(*o, i);
   a.out_pitch = o->pitch;
   a.depth_pitch = o->depth_pitch;
   a.outputs = p->outputs;
   a.warp_mode = p->warp_mode;
+  // The 2-D fill inpaints both views in place after the band kernel, so that kernel also
+  // writes both views and the holes map: into the caller's buffers when requested, else
+  // into context scratch with the same row pitches.
+  const bool inpaint = p->hole_fill == DIBR_FILL_INPAINT2D && p->warp_mode == DIBR_WARP_FORWARD;
+  if (inpaint) {
+    const uint32_t rgb = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS;
+    const uint32_t maps = DIBR_OUT_DEPTH | DIBR_OUT_HOLES;
+    const int64_t vp = (p->outputs & rgb) ? o->pitch : round_up(3 * W, 16);
+    const int64_t hp = (p->outputs & maps) ? o->depth_pitch : round_up(W, 16);
+    size_t need = 0;
+    if (!(p->outputs & DIBR_OUT_LEFT)) need += static_cast<size_t>(vp) * H;
+    if (!(p->outputs & DIBR_OUT_RIGHT)) need += static_cast<size_t>(vp) * H;
+    if (!(p->outputs & DIBR_OUT_HOLES)) need += static_cast<size_t>(hp) * H;
+    if (need && (s = ensure(inpaint_scratch, need)) != DIBR_OK) return s;
+    size_t off = 0;
+    auto take = [&](int slot, uint32_t bit, int64_t rows_pitch) {
+      if (p->outputs & bit) return;
+      a.out[slot] = inpaint_scratch.ptr + off;
+      off += static_cast<size_t>(rows_pitch) * H;
+    };
+    take(O_LEFT, DIBR_OUT_LEFT, vp);
+    take(O_RIGHT, DIBR_OUT_RIGHT, vp);
+    take(O_HOLES, DIBR_OUT_HOLES, hp);
+    a.out_pitch = vp;
+    a.depth_pitch = hp;
+    a.outputs |= DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HOLES;
+  }
   shift_tables(p, a.lut_h, a.lut_n);
   cudaError_t e = launch_band(a, smem, per_sm, stream);
   if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
   ++launches;
+  if (inpaint) {
+    InpaintArgs ia;
+    ia.view[0] = a.out[O_LEFT];
+    ia.view[1] = a.out[O_RIGHT];
+    ia.pitch = a.out_pitch;
+    ia.holes = a.out[O_HOLES];
+    ia.holes_pitch = a.depth_pitch;
+    ia.ana = (p->outputs & DIBR_OUT_ANAGLYPH) ? a.out[O_ANA] : nullptr;
+    ia.hsbs = (p->outputs & DIBR_OUT_HSBS) ? a.out[O_HSBS] : nullptr;
+    ia.out_pitch = a.out_pitch;
+    ia.W = W;
+    ia.H = H;
+    ia.block = p->inpaint_block;
+    ia.nbx = (W + ia.block - 1) / ia.block;
+    ia.nblocks = ia.nbx * ((H + ia.block - 1) / ia.block);
+    e = launch_inpaint(ia, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "inpainting launch");
+    ++launches;
+  }
   return DIBR_OK;
 }
 
@@ -370,6 +418,8 @@ dibr_status dibr_params_default(dibr_params *p) {
   p->xbf_sigma_r = 16.0f;
   p->xbf_radius = 2;
   p->outputs = DIBR_OUT_ANAGLYPH;
+  p->hole_fill = DIBR_FILL_ROW;
+  p->inpaint_block = 32;
   return DIBR_OK;
 }
 
@@ -539,31 +589,27 @@ dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params
     din.pitch = ap;
     din.on_device = 1;
   }
-  uint8_t *host_ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
   const int64_t op = round_up(3 * W, 16), dp = round_up(W, 16);
   if (!o->on_device) {
     size_t total = 0;
     size_t offs[O_COUNT];
     for (int i = 0; i < O_COUNT; ++i) {
       offs[i] = total;
-      if (p->outputs & bits[i]) total += static_cast<size_t>(i == O_DEPTH ? dp : op) * H;
+      if (p->outputs & kOutBits[i]) total += static_cast<size_t>(is_map_output(i) ? dp : op) * H;
     }
     if ((s = ensure(stage_out, total)) != DIBR_OK) return s;
-    uint8_t **dptr[O_COUNT] = {&dout.anaglyph, &dout.left, &dout.right, &dout.hsbs, &dout.depth};
-    for (int i = 0; i < O_COUNT; ++i) *dptr[i] = (p->outputs & bits[i]) ? stage_out.ptr + offs[i] : nullptr;
+    for (int i = 0; i < O_COUNT; ++i) out_slot(dout, i) = (p->outputs & kOutBits[i]) ? stage_out.ptr + offs[i] : nullptr;
     dout.pitch = op;
     dout.depth_pitch = dp;
     dout.on_device = 1;
   }
   if ((s = enqueue_device(&din, p, &dout)) != DIBR_OK) return s;
   if (!o->on_device) {
-    uint8_t *dptrs[O_COUNT] = {dout.anaglyph, dout.left, dout.right, dout.hsbs, dout.depth};
     for (int i = 0; i < O_COUNT; ++i) {
-      if (!(p->outputs & bits[i])) continue;
-      const bool dep = i == O_DEPTH;
-      e = cudaMemcpy2DAsync(host_ptrs[i], dep ? o->depth_pitch : o->pitch, dptrs[i], dep ? dp : op,
-                            dep ? static_cast<size_t>(W) : 3 * static_cast<size_t>(W), H,
+      if (!(p->outputs & kOutBits[i])) continue;
+      const bool map = is_map_output(i);
+      e = cudaMemcpy2DAsync(out_slot(*o, i), map ? o->depth_pitch : o->pitch, out_slot(dout, i), map ? dp : op,
+                            map ? static_cast<size_t>(W) : 3 * static_cast<size_t>(W), H,
                             cudaMemcpyDeviceToHost, stream);
       if (e != cudaSuccess) return cuda_fail(e, "output download");
     }
@@ -572,7 +618,7 @@ dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params
 }
 
 void dibr_ctx::release_buffers() {
-  for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth}) {
+  for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth, &inpaint_scratch}) {
     dev_free(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;

@@ -222,8 +222,9 @@ __device__ __noinline__ int warp_walk_right(const uint32_t *zb, int t, int W, in
 // warp's 512 targets, from a warp-wide search of the z-buffer.  A missing right key
 // carries in as 0, which is never strictly farther; holes with no left key (row starts)
 // are set afterwards on a path of their own.
-__device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0, int npx, int W,
-                                             int lane, int warp_lo, int warp_hi, uint32_t (&k)[16]) {
+// Returns the thread's hole bits (bit j: no source reached target x0 + j).
+__device__ __forceinline__ uint32_t resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0, int npx, int W,
+                                                 int lane, int warp_lo, int warp_hi, uint32_t (&k)[16]) {
   const uint32_t zs = smem_addr(zb);
   if (npx > 0) {
 #pragma unroll
@@ -242,7 +243,7 @@ __device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *
     if (k[i] != kEmpty) m |= 1u << i;
   m &= rowmask;
   const uint32_t holes = ~m & rowmask;
-  if (!__any_sync(0xffffffffu, holes != 0u)) return;
+  if (!__any_sync(0xffffffffu, holes != 0u)) return holes;
 
   const int first = m ? x0 + __ffs(m) - 1 : kNoTarget;  // this chunk's first / last filled target
   const int last = m ? x0 + 31 - __clz(m) : -1;
@@ -281,15 +282,22 @@ __device__ __forceinline__ void resolve_view(const uint32_t *zb, const uint8_t *
     else if (c > (k[j] | 0xFFFFFFu)) k[j] = c;
   }
   // holes before the first filled target of the row: the right key, or the input pixel
-  // when the row has no filled target
+  // when the row has no filled target at all
   const bool row_start = nl < 0 && before != 0u;
   if (__any_sync(0xffffffffu, row_start) && row_start) {
     const int r = m ? first : nr;
-    const uint32_t cr = r < W ? lds_u32(zs + 4u * r) : kEmpty;
+    if (r < W) {
+      const uint32_t cr = lds_u32(zs + 4u * r);
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
-      if ((before >> j) & 1u) k[j] = cr != kEmpty ? cr : rgb_at(rgbrow, x0 + j);
+      for (int j = 0; j < 16; ++j)
+        if ((before >> j) & 1u) k[j] = cr;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)  // (no bit is set past the row's end)
+        if ((before >> j) & 1u) k[j] = rgb_at(rgbrow, x0 + j);
+    }
   }
+  return holes;
 }
 
 // Rounded-up per-byte mean of two packed colours: (a + b + 1) >> 1 in every byte.
@@ -470,6 +478,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   };
 
   const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
+  const bool want_holes = (a.outputs & DIBR_OUT_HOLES) != 0;
   const bool want_ana = (a.outputs & DIBR_OUT_ANAGLYPH) != 0;
   const bool want_l = (a.outputs & DIBR_OUT_LEFT) != 0;
   const bool want_r = (a.outputs & DIBR_OUT_RIGHT) != 0;
@@ -608,9 +617,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 
     // ---- phase C: resolve winners, fill holes, compose and store the outputs
     uint32_t kl[16], kr[16];
+    uint32_t hole_l = 0u, hole_r = 0u;
     if (forward) {
-      resolve_view(zl, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kl);
-      resolve_view(zr, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kr);
+      hole_l = resolve_view(zl, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kl);
+      hole_r = resolve_view(zr, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kr);
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
 #pragma unroll
@@ -623,6 +633,16 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         kl[i] = active ? rgb_at(rgbrow, sl) : 0u;
         kr[i] = active ? rgb_at(rgbrow, sr) : 0u;
       }
+    }
+    if (active && want_holes) {
+      // one byte per target: bit 0 a hole of the left view, bit 1 of the right view
+      auto spread4 = [](uint32_t x) { return ((x & 0xFu) * 0x00204081u) & 0x01010101u; };
+      uint4 hv;
+      hv.x = spread4(hole_l) | (spread4(hole_r) << 1);
+      hv.y = spread4(hole_l >> 4) | (spread4(hole_r >> 4) << 1);
+      hv.z = spread4(hole_l >> 8) | (spread4(hole_r >> 8) << 1);
+      hv.w = spread4(hole_l >> 12) | (spread4(hole_r >> 12) << 1);
+      store16(a.out[O_HOLES] + static_cast<int64_t>(y) * a.depth_pitch + x0, hv, npx);
     }
     if (active) {
       const int64_t ro = static_cast<int64_t>(y) * a.out_pitch;

@@ -148,11 +148,7 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
     d.in_pitch = in_pitch[i];
     d.depth_in = depth_in[i];
     d.depth_in_pitch = depth_pitch_in[i];
-    d.out[O_ANA] = o.anaglyph;
-    d.out[O_LEFT] = o.left;
-    d.out[O_RIGHT] = o.right;
-    d.out[O_HSBS] = o.hsbs;
-    d.out[O_DEPTH] = o.depth;
+    for (int k = 0; k < O_COUNT; ++k) d.out[k] = out_slot(o, k);
     d.out_pitch = o.pitch;
     d.depth_pitch = o.depth_pitch;
     d.W = im.width;
@@ -216,6 +212,10 @@ static dibr_status check_batch(dibr_ctx *c, int n, const dibr_image *imgs, const
       c->set_error("image %d: %s", i, why.c_str());
       return s;
     }
+    if (p[n_params == 1 ? 0 : i].hole_fill != DIBR_FILL_ROW) {
+      c->set_error("image %d: the 2-D fill runs on single-image calls only", i);
+      return DIBR_E_INVALID;
+    }
   }
   return DIBR_OK;
 }
@@ -244,14 +244,14 @@ dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, co
   std::vector<dibr_image> di(imgs, imgs + n);
   std::vector<dibr_outputs> dout(outs, outs + n);
   size_t need = 0;
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  const uint32_t *bits = kOutBits;
   for (int i = 0; i < n; ++i) {
     const dibr_params &pp = p[n_params == 1 ? 0 : i];
     if (!imgs[i].on_device) need += static_cast<size_t>(round_up(3 * imgs[i].width, 16)) * imgs[i].height;
     if (!outs[i].on_device)
       for (int k = 0; k < O_COUNT; ++k)
         if (pp.outputs & bits[k])
-          need += static_cast<size_t>(round_up(k == O_DEPTH ? imgs[i].width : 3 * imgs[i].width, 16)) * imgs[i].height;
+          need += static_cast<size_t>(round_up(is_map_output(k) ? imgs[i].width : 3 * imgs[i].width, 16)) * imgs[i].height;
   }
   if (need && (s = c->ensure(c->stage_in, need)) != DIBR_OK) return s;
   size_t off = 0;
@@ -269,12 +269,11 @@ dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, co
       off += static_cast<size_t>(ap) * H;
     }
     if (!outs[i].on_device) {
-      uint8_t **dp[O_COUNT] = {&dout[i].anaglyph, &dout[i].left, &dout[i].right, &dout[i].hsbs, &dout[i].depth};
       const int64_t op = round_up(3 * W, 16), dpp = round_up(W, 16);
       for (int k = 0; k < O_COUNT; ++k) {
         if (!(pp.outputs & bits[k])) continue;
-        *dp[k] = c->stage_in.ptr + off;
-        off += static_cast<size_t>(k == O_DEPTH ? dpp : op) * H;
+        out_slot(dout[i], k) = c->stage_in.ptr + off;
+        off += static_cast<size_t>(is_map_output(k) ? dpp : op) * H;
       }
       dout[i].pitch = op;
       dout[i].depth_pitch = dpp;
@@ -287,12 +286,10 @@ dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, co
     if (outs[i].on_device) continue;
     const dibr_params &pp = p[n_params == 1 ? 0 : i];
     const int W = imgs[i].width, H = imgs[i].height;
-    const uint8_t *src[O_COUNT] = {dout[i].anaglyph, dout[i].left, dout[i].right, dout[i].hsbs, dout[i].depth};
-    uint8_t *dst[O_COUNT] = {outs[i].anaglyph, outs[i].left, outs[i].right, outs[i].hsbs, outs[i].depth};
     for (int k = 0; k < O_COUNT && e == cudaSuccess; ++k) {
       if (!(pp.outputs & bits[k])) continue;
-      const bool dep = k == O_DEPTH;
-      e = cudaMemcpy2DAsync(dst[k], dep ? outs[i].depth_pitch : outs[i].pitch, src[k],
+      const bool dep = is_map_output(k);
+      e = cudaMemcpy2DAsync(out_slot(outs[i], k), dep ? outs[i].depth_pitch : outs[i].pitch, out_slot(dout[i], k),
                             dep ? dout[i].depth_pitch : dout[i].pitch, dep ? W : 3 * static_cast<size_t>(W), H,
                             cudaMemcpyDeviceToHost, c->stream);
     }

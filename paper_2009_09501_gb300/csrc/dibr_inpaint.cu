@@ -1,0 +1,270 @@
+// dibr_inpaint.cu -- the iterative 2-D block inpainting of Fig. 3 (left column), run over
+// the holes of both reconstructed views after the band kernel (hole fill DIBR_FILL_INPAINT2D).
+//
+// Per block of B x B pixels and per view, one warp.  The figure's algorithm visits the
+// block's damaged pixels block column by block column, repeatedly, and repairs a pixel
+// once two or more of its 8 neighbours are undamaged; a repair is visible at once to the
+// pixels visited after it.  The warp runs that sequential order as a wavefront: lane x
+// owns block column x and at step s handles row s - 2x.  Along the visiting order every
+// neighbour of (x, y) that comes earlier -- column x-1 entirely, and (x, y-1) -- has a
+// smaller step (2x + y - 1 or less), every later one -- column x+1, and (x, y+1) -- a
+// larger step, and no two neighbours share a step; so each step sees exactly the state
+// the sequential visit would see, and the result is the same.
+//
+// The damage flags of a column live in a 64-bit register of its lane (bit j = block row
+// j - 1, with the rows above and below the block at bits 0 and B + 1); a lane reads its
+// neighbours' columns with shuffles at the step it needs them.  Colours live in shared
+// memory with a one-pixel frame around the block.  Pixels outside the block are read as
+// the band kernel left them (they are never written by this block, and their damage
+// flags come from the holes map, which nothing changes), so blocks are independent.
+// Repaired pixels are written back into the view in place; then the anaglyph and HSBS
+// outputs are rewritten where a view changed.
+#include "dibr_internal.h"
+
+namespace dibr {
+namespace {
+
+constexpr int kMaxBlock = 32;
+constexpr int kStride = kMaxBlock + 2;  // cells per row of a block's colour frame
+constexpr int kBlocksPerCta = 4;        // image blocks per CTA; one warp per block and view
+
+// floor(v / (2n)) for v < 4096 and n = 2..8 as (v * ceil(65536 / 2n)) >> 16 (exact over that
+// range); index n.
+__constant__ uint32_t kHalfRecip[9] = {0, 0, 16384, 10923, 8192, 6554, 5462, 4682, 4096};
+
+__device__ __forceinline__ uint32_t load_rgb(const uint8_t *p) {
+  return static_cast<uint32_t>(p[0]) | (static_cast<uint32_t>(p[1]) << 8) | (static_cast<uint32_t>(p[2]) << 16);
+}
+
+__device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
+  p[0] = static_cast<uint8_t>(c);
+  p[1] = static_cast<uint8_t>(c >> 8);
+  p[2] = static_cast<uint8_t>(c >> 16);
+}
+
+__global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
+  __shared__ uint32_t cells[kBlocksPerCta][2][kStride * kStride];
+  __shared__ uint64_t repaired[kBlocksPerCta][2][kMaxBlock];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = warp >> 1, v = warp & 1;
+  const int blk = blockIdx.x * kBlocksPerCta + q;
+  const int B = a.block, W = a.W, H = a.H;
+  int bx0 = 0, by0 = 0, bw = 0, bh = 0;
+  if (blk < a.nblocks) {
+    bx0 = (blk % a.nbx) * B;
+    by0 = (blk / a.nbx) * B;
+    bw = min(B, W - bx0);
+    bh = min(B, H - by0);
+  }
+  uint8_t *view = a.view[v];
+  const uint32_t vbit = 1u << v;
+  uint32_t *cell = cells[q][v];
+
+  // ---- this view's holes inside the block (lane x: column x), every row's load in flight
+  uint64_t own = 0;
+  {
+    // (addresses of lanes and rows outside the block are clamped to the block's corner)
+    const uint8_t *hp = a.holes + static_cast<int64_t>(by0) * a.holes_pitch + bx0 + (lane < bw ? lane : 0);
+    uint32_t hb[kMaxBlock];
+#pragma unroll
+    for (int r = 0; r < kMaxBlock; ++r) {
+      const bool in = lane < bw && r < bh;
+      const uint32_t v8 = hp[static_cast<int64_t>(r < bh ? r : 0) * a.holes_pitch];
+      hb[r] = in ? v8 : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kMaxBlock; ++r)
+      if (hb[r] & vbit) own |= 2ull << r;
+  }
+  const bool work = __any_sync(0xffffffffu, own != 0);
+  uint64_t own0 = own;
+  if (work) {
+    // ---- colours of the block and its one-pixel frame, damage flags of the frame
+    // (pixels outside the image count as damaged); eight rows of loads in flight at a time
+    uint64_t col_a = 0, col_b = 0;  // flags of frame columns lane and lane + 32
+    for (int i = lane; i < bw + 2; i += 32) {
+      const int x = bx0 - 1 + i;
+      const bool xin = x >= 0 && x < W;
+      uint64_t flags = 0;
+      for (int j0 = 0; j0 < bh + 2; j0 += 8) {
+        uint32_t hv[8], c0[8], c1[8], c2[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + t, y = by0 - 1 + j;
+          const bool in = xin && j < bh + 2 && y >= 0 && y < H;
+          const int64_t yy = in ? y : by0, xx = in ? x : bx0;  // pixels outside: read (bx0, by0), unused
+          const uint8_t *px = view + yy * a.pitch + 3 * xx;
+          const uint32_t h8 = a.holes[yy * a.holes_pitch + xx];
+          hv[t] = in ? h8 : 0xFFu;
+          c0[t] = px[0];
+          c1[t] = px[1];
+          c2[t] = px[2];
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + t;
+          if (j >= bh + 2) break;
+          const bool bad = (hv[t] & vbit) != 0;
+          cell[j * kStride + i] = bad ? 0u : (c0[t] | (c1[t] << 8) | (c2[t] << 16));
+          if (bad) flags |= 1ull << j;
+        }
+      }
+      if (i < 32) col_a = flags;
+      else col_b = flags;
+    }
+    // lane x (< bw) owns frame column x + 1; the frame columns 0 and bw + 1 are the halo
+    const uint64_t next_a = __shfl_sync(0xffffffffu, col_a, (lane + 1) & 31);
+    const uint64_t first_b = __shfl_sync(0xffffffffu, col_b, 0);
+    own = lane < bw ? (lane < 31 ? next_a : first_b) : ~0ull;
+    own0 = own;
+    const uint64_t halo_l = __shfl_sync(0xffffffffu, col_a, 0);
+    const int hr = bw + 1;
+    const uint64_t hr_a = __shfl_sync(0xffffffffu, col_a, hr & 31);
+    const uint64_t hr_b = __shfl_sync(0xffffffffu, col_b, hr & 31);
+    const uint64_t halo_r = hr < 32 ? hr_a : hr_b;
+    __syncwarp();
+
+    const uint64_t rows = ((1ull << bh) - 1ull) << 1;  // the block's own rows in a column mask
+    // A damaged pixel whose neighbourhood has not changed since it last failed the test
+    // fails it again, so a visit only checks "dirty" pixels: all of them in the first pass,
+    // then those next to a pixel repaired since their last check.  The result is the same
+    // as checking every damaged pixel; the work follows the repair front.
+    uint64_t dirty = lane < bw ? own & rows : 0ull;
+    uint64_t lm = __shfl_up_sync(0xffffffffu, own, 1);
+    uint64_t rm = __shfl_down_sync(0xffffffffu, own, 1);
+    if (lane == 0) lm = halo_l;
+    if (lane == bw - 1) rm = halo_r;
+    // the steps at which some lane visits a dirty damaged pixel: lane x visits block row r
+    // at step 2x + r (steps 0..93, three words)
+    auto active = [&](uint32_t (&act)[3]) {
+      const uint64_t dm = lane < bw ? (own & dirty & rows) >> 1 : 0ull;
+      const int sh = 2 * lane;
+      const uint64_t lo = dm << sh, hi = sh ? dm >> (64 - sh) : 0ull;
+      act[0] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo));
+      act[1] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo >> 32));
+      act[2] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(hi));
+    };
+    // passes over the block in the visiting order, while a pass repairs something
+    while (true) {
+      uint32_t act[3];
+      active(act);
+      bool fixed = false;
+      for (int w = 0; w < 3; ++w) {
+        while (act[w]) {
+          const int s = 32 * w + __ffs(act[w]) - 1;
+          act[w] &= act[w] - 1;
+          const int r = s - 2 * lane;  // block row this lane visits at step s
+          const bool cand = lane < bw && r >= 0 && r < bh && ((own & dirty) >> (r + 1)) & 1ull;
+          bool rep = false;
+          if (cand) {
+            dirty &= ~(1ull << (r + 1));
+            // frame rows r, r + 1 (the pixel's own), r + 2 of the three columns
+            const uint32_t bl = static_cast<uint32_t>(lm >> r) & 7u;
+            const uint32_t bo = static_cast<uint32_t>(own >> r) & 5u;
+            const uint32_t br = static_cast<uint32_t>(rm >> r) & 7u;
+            const int n = 8 - __popc(bl) - __popc(bo) - __popc(br);
+            if (n >= 2) {
+              uint32_t sr = 0, sg = 0, sb = 0;
+#pragma unroll
+              for (int dj = 0; dj < 3; ++dj) {
+#pragma unroll
+                for (int di = 0; di < 3; ++di) {
+                  const uint32_t m = di == 0 ? bl : di == 1 ? bo : br;
+                  if (di == 1 && dj == 1) continue;
+                  if ((m >> dj) & 1u) continue;
+                  const uint32_t c = cell[(r + dj) * kStride + lane + di];
+                  sr += c & 0xFFu;
+                  sg += (c >> 8) & 0xFFu;
+                  sb += c >> 16;
+                }
+              }
+              // per channel floor((2 sum + n) / 2n): the mean rounded half up
+              const uint32_t rc = kHalfRecip[n];
+              const uint32_t c = (((2u * sr + n) * rc) >> 16) | ((((2u * sg + n) * rc) >> 16) << 8) |
+                                 ((((2u * sb + n) * rc) >> 16) << 16);
+              cell[(r + 1) * kStride + lane + 1] = c;
+              own &= ~(1ull << (r + 1));
+              rep = true;
+            }
+          }
+          __syncwarp();
+          if (__any_sync(0xffffffffu, rep)) {
+            // new neighbour columns; their damaged neighbours (and this column's) become dirty
+            uint64_t nl = __shfl_up_sync(0xffffffffu, own, 1);
+            uint64_t nr = __shfl_down_sync(0xffffffffu, own, 1);
+            if (lane == 0) nl = halo_l;
+            if (lane == bw - 1) nr = halo_r;
+            const uint64_t gone = (lm & ~nl) | (rm & ~nr) | (rep ? 1ull << (r + 1) : 0ull);
+            lm = nl;
+            rm = nr;
+            dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
+            fixed = true;
+            // a repair at step s can make pixels later in this pass dirty only at steps
+            // s + 1 (the next row of its column) .. s + 3 (the next column's three rows)
+            if (s + 1 < 96) act[(s + 1) >> 5] |= 1u << ((s + 1) & 31);
+            if (s + 2 < 96) act[(s + 2) >> 5] |= 1u << ((s + 2) & 31);
+            if (s + 3 < 96) act[(s + 3) >> 5] |= 1u << ((s + 3) & 31);
+          }
+        }
+      }
+      if (!fixed || !__any_sync(0xffffffffu, lane < bw && (own & rows) != 0)) break;
+    }
+    // ---- repaired pixels back into the view
+    const uint64_t rep = lane < bw ? (own0 & ~own & rows) : 0ull;
+    uint64_t left = rep;
+    while (left) {
+      const int j = __ffsll(static_cast<long long>(left)) - 1;  // frame row; block row j - 1
+      left &= left - 1;
+      store_rgb(view + static_cast<int64_t>(by0 + j - 1) * a.pitch + 3 * static_cast<int64_t>(bx0 + lane),
+                cell[j * kStride + lane + 1]);
+    }
+    repaired[q][v][lane] = rep;
+  } else {
+    repaired[q][v][lane] = 0ull;
+  }
+  __syncthreads();  // both views of every block of this CTA are final in memory
+
+  // ---- formatted outputs where a view changed
+  const uint64_t rl = repaired[q][0][lane], rr = repaired[q][1][lane];
+  const uint64_t mine = v == 0 ? rl : rr;
+  const uint64_t pair = mine | __shfl_down_sync(0xffffffffu, mine, 1);  // rows where x or x + 1 changed
+  if (lane < bw) {
+    const int x = bx0 + lane;
+    if (v == 0 && a.ana) {
+      uint64_t m = rl | rr;
+      while (m) {
+        const int j = __ffsll(static_cast<long long>(m)) - 1;
+        m &= m - 1;
+        const int64_t o = static_cast<int64_t>(by0 + j - 1) * a.pitch + 3 * static_cast<int64_t>(x);
+        uint8_t *d = a.ana + static_cast<int64_t>(by0 + j - 1) * a.out_pitch + 3 * static_cast<int64_t>(x);
+        d[0] = a.view[0][o];
+        d[1] = a.view[1][o + 1];
+        d[2] = a.view[1][o + 2];
+      }
+    }
+    if (a.hsbs && (lane & 1) == 0) {
+      // pairs (x, x + 1) of this view; blocks start at even columns and have even widths
+      uint64_t m = pair;
+      const uint8_t *src = a.view[v];
+      while (m) {
+        const int j = __ffsll(static_cast<long long>(m)) - 1;
+        m &= m - 1;
+        const int y = by0 + j - 1;
+        const uint8_t *p = src + static_cast<int64_t>(y) * a.pitch + 3 * static_cast<int64_t>(x);
+        uint8_t *d = a.hsbs + static_cast<int64_t>(y) * a.out_pitch + 3 * static_cast<int64_t>((v ? W / 2 : 0) + x / 2);
+        for (int c = 0; c < 3; ++c) d[c] = static_cast<uint8_t>((p[c] + p[3 + c] + 1) >> 1);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st) {
+  if (a.nblocks <= 0) return cudaSuccess;
+  const int grid = (a.nblocks + kBlocksPerCta - 1) / kBlocksPerCta;
+  inpaint_kernel<<<grid, 32 * 2 * kBlocksPerCta, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace dibr

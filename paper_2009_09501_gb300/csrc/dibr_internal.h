@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dibr.h"
+
 namespace dibr {
 
 constexpr int kChunk = 16;          // pixels owned by one consumer thread per pass
@@ -33,8 +35,22 @@ enum LoadMode : int {
 // Bits of the device status word.
 enum : int { ST_TIMEOUT_FULL = 1, ST_TIMEOUT_EMPTY = 2, ST_BAD_ARGS = 4, ST_TIMEOUT_DRAIN = 8 };
 
-// Output slots, in the order of dibr_outputs.
-enum { O_ANA = 0, O_LEFT = 1, O_RIGHT = 2, O_HSBS = 3, O_DEPTH = 4, O_COUNT = 5 };
+// Output slots, in the order of dibr_outputs; depth and holes are one-byte maps (row
+// pitch depth_pitch), the others RGB (row pitch pitch).
+enum { O_ANA = 0, O_LEFT = 1, O_RIGHT = 2, O_HSBS = 3, O_DEPTH = 4, O_HOLES = 5, O_COUNT = 6 };
+constexpr uint32_t kOutBits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT,
+                                        DIBR_OUT_HSBS,     DIBR_OUT_DEPTH, DIBR_OUT_HOLES};
+constexpr uint32_t kAllOutputs =
+    DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS | DIBR_OUT_DEPTH | DIBR_OUT_HOLES;
+__host__ __device__ constexpr bool is_map_output(int i) { return i == O_DEPTH || i == O_HOLES; }
+inline uint8_t *&out_slot(dibr_outputs &o, int i) {
+  uint8_t **s[O_COUNT] = {&o.anaglyph, &o.left, &o.right, &o.hsbs, &o.depth, &o.holes};
+  return *s[i];
+}
+inline uint8_t *out_slot(const dibr_outputs &o, int i) {
+  uint8_t *const s[O_COUNT] = {o.anaglyph, o.left, o.right, o.hsbs, o.depth, o.holes};
+  return s[i];
+}
 
 // Per-image arguments of the band kernel.  The tensor map comes first for its 64-byte
 // alignment; the kernel receives the whole record as a __grid_constant__ parameter.
@@ -212,12 +228,25 @@ inline void order_by_area(int n, const int *width, const int *height, int *order
   }
 }
 
-// Host launchers (dibr_band.cu, dibr_xbf.cu).
+// Arguments of the 2-D block inpainting (dibr_inpaint.cu): both views are repaired in
+// place; anaglyph and HSBS (either may be null) are rewritten where a view changed.
+struct InpaintArgs {
+  uint8_t *view[2];       // left, right: row-filled views, W x H x 3, row pitch `pitch`
+  int64_t pitch;
+  const uint8_t *holes;   // bit 0: hole of the left view, bit 1: of the right view
+  int64_t holes_pitch;
+  uint8_t *ana, *hsbs;    // row pitch out_pitch
+  int64_t out_pitch;
+  int32_t W, H, block, nbx, nblocks;
+};
+
+// Host launchers (dibr_band.cu, dibr_xbf.cu, dibr_inpaint.cu).
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st);
 // chained: may start while the previous launch on the stream finishes (the previous
 // launch is a batch launch of the same call).
 cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st);
 int band_max_threads(int ctas_per_sm);
+cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st);
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,
                        cudaStream_t st);

@@ -92,9 +92,8 @@ struct ServeState {
 
 static size_t stream_bytes(const Stream &s) {
   size_t b = static_cast<size_t>(s.in_pitch) * s.H;
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
   for (int k = 0; k < O_COUNT; ++k)
-    if (s.p.outputs & bits[k]) b += static_cast<size_t>(k == O_DEPTH ? s.depth_pitch : s.out_pitch) * s.H;
+    if (s.p.outputs & kOutBits[k]) b += static_cast<size_t>(is_map_output(k) ? s.depth_pitch : s.out_pitch) * s.H;
   return b * kSlots;
 }
 
@@ -113,7 +112,7 @@ static void free_stream(ServeState *st, Stream &s) {
 // Scheduler: forms and enqueues batches.
 static void scheduler_loop(ServeState *st) {
   cudaSetDevice(st->gpu->device);
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  const uint32_t *bits = kOutBits;
   std::vector<dibr_image> imgs;
   std::vector<dibr_params> prms;
   std::vector<dibr_outputs> outs;
@@ -167,11 +166,7 @@ static void scheduler_loop(ServeState *st) {
         prms.push_back(s.p);
         dibr_outputs o;
         std::memset(&o, 0, sizeof(o));
-        o.anaglyph = sl.out[O_ANA];
-        o.left = sl.out[O_LEFT];
-        o.right = sl.out[O_RIGHT];
-        o.hsbs = sl.out[O_HSBS];
-        o.depth = sl.out[O_DEPTH];
+        for (int k = 0; k < O_COUNT; ++k) out_slot(o, k) = sl.out[k];
         o.pitch = s.out_pitch;
         o.depth_pitch = s.depth_pitch;
         o.on_device = 1;
@@ -200,12 +195,10 @@ static void scheduler_loop(ServeState *st) {
     cudaStreamWaitEvent(st->d2h, comp, 0);
     for (size_t f = 0; f < b.frames.size() && status == DIBR_OK; ++f) {
       const Frame &fr = b.meta[f];
-      const uint8_t *src[O_COUNT] = {outs[f].anaglyph, outs[f].left, outs[f].right, outs[f].hsbs, outs[f].depth};
-      uint8_t *dst[O_COUNT] = {fr.out.anaglyph, fr.out.left, fr.out.right, fr.out.hsbs, fr.out.depth};
       for (int k = 0; k < O_COUNT; ++k) {
         if (!(prms[f].outputs & bits[k])) continue;
-        const bool dep = k == O_DEPTH;
-        if (cudaMemcpy2DAsync(dst[k], dep ? fr.out.depth_pitch : fr.out.pitch, src[k],
+        const bool dep = is_map_output(k);
+        if (cudaMemcpy2DAsync(out_slot(fr.out, k), dep ? fr.out.depth_pitch : fr.out.pitch, out_slot(outs[f], k),
                               dep ? outs[f].depth_pitch : outs[f].pitch,
                               dep ? imgs[f].width : 3 * static_cast<size_t>(imgs[f].width), imgs[f].height,
                               cudaMemcpyDeviceToHost, st->d2h) != cudaSuccess)
@@ -349,13 +342,17 @@ dibr_status dibr_open_stream(dibr_ctx *c, int width, int height, const dibr_para
   dibr_outputs po;
   std::memset(&po, 0, sizeof(po));
   uint8_t *nonnull = reinterpret_cast<uint8_t *>(16);
-  po.anaglyph = po.left = po.right = po.hsbs = po.depth = nonnull;
+  for (int k = 0; k < O_COUNT; ++k) out_slot(po, k) = nonnull;
   po.pitch = 3 * static_cast<int64_t>(width);
   po.depth_pitch = width;
   dibr_status s = check_image_args(p, &probe, &po, &why);
   if (s != DIBR_OK) {
     c->set_error("%s", why.c_str());
     return s;
+  }
+  if (p->hole_fill != DIBR_FILL_ROW) {
+    c->set_error("the 2-D fill runs on single-image calls only");
+    return DIBR_E_INVALID;
   }
   cudaSetDevice(c->device);
   if ((s = ensure_serving(c)) != DIBR_OK) return s;
@@ -381,7 +378,7 @@ dibr_status dibr_open_stream(dibr_ctx *c, int width, int height, const dibr_para
                  static_cast<unsigned long long>(st->resident), static_cast<unsigned long long>(c->mem_budget));
     return DIBR_E_BUSY;
   }
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
+  const uint32_t *bits = kOutBits;
   bool ok = true;
   for (Slot &sl : strm->slots) {
     sl.in = static_cast<uint8_t *>(st->gpu->dev_alloc(static_cast<size_t>(strm->in_pitch) * height));
@@ -389,7 +386,7 @@ dibr_status dibr_open_stream(dibr_ctx *c, int width, int height, const dibr_para
     for (int k = 0; k < O_COUNT; ++k)
       if (p->outputs & bits[k]) {
         sl.out[k] = static_cast<uint8_t *>(
-            st->gpu->dev_alloc(static_cast<size_t>(k == O_DEPTH ? strm->depth_pitch : strm->out_pitch) * height));
+            st->gpu->dev_alloc(static_cast<size_t>(is_map_output(k) ? strm->depth_pitch : strm->out_pitch) * height));
         ok = ok && sl.out[k];
       }
   }

@@ -78,20 +78,19 @@ bool valid_image(const dibr_params *p, const dibr_image *im, const dibr_outputs 
   if (p->disparity_rule < 0 || p->disparity_rule > 1 || p->warp_mode < 0 || p->warp_mode > 1) return false;
   if (p->warp_mode == DIBR_WARP_GATHER_FIG3 && p->disparity_rule != DIBR_DISP_PAPER) return false;
   if (p->max_parallax_px < 0 || p->max_parallax_px > 1024 || p->threshold < 0 || p->threshold > 255) return false;
-  const uint32_t all = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS | DIBR_OUT_DEPTH;
-  if (p->outputs == 0 || (p->outputs & ~all)) return false;
+  if (p->outputs == 0 || (p->outputs & ~kAllOutputs)) return false;
+  if (p->hole_fill != DIBR_FILL_ROW) return false;  // the 2-D fill needs scratch views
   if (!im->rgb || !im->on_device || !o->on_device) return false;
   if (im->width < 1 || im->height < 1 || im->width > kMaxWidth || im->height > 65535) return false;
   if (im->pitch < 3 * static_cast<int64_t>(im->width)) return false;
   // rows are read with one bulk copy each: 16-byte aligned rows of whole 16-byte units
   if ((reinterpret_cast<uintptr_t>(im->rgb) & 15u) || (im->pitch & 15) || (3 * im->width) % 16) return false;
   if ((p->outputs & DIBR_OUT_HSBS) && (im->width & 1)) return false;
-  const uint8_t *ptrs[O_COUNT] = {o->anaglyph, o->left, o->right, o->hsbs, o->depth};
-  const uint32_t bits[O_COUNT] = {DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH};
   for (int k = 0; k < O_COUNT; ++k)
-    if ((p->outputs & bits[k]) && !ptrs[k]) return false;
-  if ((p->outputs & ~DIBR_OUT_DEPTH) && o->pitch < 3 * static_cast<int64_t>(im->width)) return false;
-  if ((p->outputs & DIBR_OUT_DEPTH) && o->depth_pitch < im->width) return false;
+    if ((p->outputs & kOutBits[k]) && !out_slot(*o, k)) return false;
+  const uint32_t maps = DIBR_OUT_DEPTH | DIBR_OUT_HOLES;
+  if ((p->outputs & ~maps) && o->pitch < 3 * static_cast<int64_t>(im->width)) return false;
+  if ((p->outputs & maps) && o->depth_pitch < im->width) return false;
   return true;
 }
 
@@ -149,11 +148,7 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     std::memset(&dd, 0, sizeof(dd));
     dd.in = im.rgb;
     dd.in_pitch = im.pitch;
-    dd.out[O_ANA] = o.anaglyph;
-    dd.out[O_LEFT] = o.left;
-    dd.out[O_RIGHT] = o.right;
-    dd.out[O_HSBS] = o.hsbs;
-    dd.out[O_DEPTH] = o.depth;
+    for (int k = 0; k < O_COUNT; ++k) dd.out[k] = out_slot(o, k);
     dd.out_pitch = o.pitch;
     dd.depth_pitch = o.depth_pitch;
     dd.W = im.width;

@@ -19,8 +19,10 @@ STATUS_NAMES = {0: "DIBR_OK", 1: "DIBR_NOT_READY", -1: "DIBR_E_INVALID", -2: "DI
 DIBR_DEPTH_LUMA, DIBR_DEPTH_LUMA_BINOM5, DIBR_DEPTH_LUMA_XBF = 0, 1, 2
 DIBR_DISP_PAPER, DIBR_DISP_LINEAR = 0, 1
 DIBR_WARP_FORWARD, DIBR_WARP_GATHER_FIG3 = 0, 1
-DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH = 1, 2, 4, 8, 16
-OUTPUT_BITS = {"anaglyph": 1, "left": 2, "right": 4, "hsbs": 8, "depth": 16}
+DIBR_OUT_ANAGLYPH, DIBR_OUT_LEFT, DIBR_OUT_RIGHT, DIBR_OUT_HSBS, DIBR_OUT_DEPTH, DIBR_OUT_HOLES = 1, 2, 4, 8, 16, 32
+OUTPUT_BITS = {"anaglyph": 1, "left": 2, "right": 4, "hsbs": 8, "depth": 16, "holes": 32}
+MAP_OUTPUTS = ("depth", "holes")  # one byte per pixel, row pitch depth_pitch
+DIBR_FILL_ROW, DIBR_FILL_INPAINT2D = 0, 1
 
 # exported symbols, as declared in include/dibr.h
 SYMBOLS = ("dibr_params_default", "dibr_validate", "dibr_shift_tables", "dibr_create",
@@ -34,7 +36,7 @@ class dibr_params(C.Structure):
     _fields_ = [("depth_rule", C.c_int32), ("disparity_rule", C.c_int32), ("warp_mode", C.c_int32),
                 ("max_parallax_px", C.c_int32), ("threshold", C.c_int32),
                 ("xbf_sigma_s", C.c_float), ("xbf_sigma_r", C.c_float), ("xbf_radius", C.c_int32),
-                ("outputs", C.c_uint32)]
+                ("outputs", C.c_uint32), ("hole_fill", C.c_int32), ("inpaint_block", C.c_int32)]
 
 
 class dibr_image(C.Structure):
@@ -44,8 +46,8 @@ class dibr_image(C.Structure):
 
 class dibr_outputs(C.Structure):
     _fields_ = [("anaglyph", C.c_void_p), ("left", C.c_void_p), ("right", C.c_void_p),
-                ("hsbs", C.c_void_p), ("depth", C.c_void_p), ("pitch", C.c_int64),
-                ("depth_pitch", C.c_int64), ("on_device", C.c_int32)]
+                ("hsbs", C.c_void_p), ("depth", C.c_void_p), ("holes", C.c_void_p),
+                ("pitch", C.c_int64), ("depth_pitch", C.c_int64), ("on_device", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -209,10 +211,12 @@ def dibr_synthesize_batch_static(n, imgs, p, n_params, outs, stream):
 # ------------------------------------------------------------------ convenience layer
 def make_params(depth_rule=DIBR_DEPTH_LUMA_BINOM5, disparity_rule=DIBR_DISP_PAPER,
                 warp_mode=DIBR_WARP_FORWARD, max_parallax=16, threshold=150, xbf_sigma_s=1.5,
-                xbf_sigma_r=16.0, xbf_radius=2, outputs=("anaglyph",)):
+                xbf_sigma_r=16.0, xbf_radius=2, outputs=("anaglyph",), hole_fill=DIBR_FILL_ROW,
+                inpaint_block=32):
     p = dibr_params()
     dibr_params_default(p)
     p.depth_rule, p.disparity_rule, p.warp_mode = depth_rule, disparity_rule, warp_mode
+    p.hole_fill, p.inpaint_block = hole_fill, inpaint_block
     p.max_parallax_px, p.threshold = max_parallax, threshold
     p.xbf_sigma_s, p.xbf_sigma_r, p.xbf_radius = xbf_sigma_s, xbf_sigma_r, xbf_radius
     bits = 0
@@ -262,7 +266,9 @@ def outputs_struct(outs, pitch=None, depth_pitch=None):
         if dev is not None and d != dev:
             raise ValueError("outputs must be all host or all device buffers")
         dev = d
-        if name == "depth":
+        if name in MAP_OUTPUTS:
+            if o.depth_pitch and o.depth_pitch != (depth_pitch if depth_pitch is not None else st):
+                raise ValueError("depth and holes maps must share one row pitch")
             o.depth_pitch = depth_pitch if depth_pitch is not None else st
         else:
             o.pitch = pitch if pitch is not None else st

@@ -37,7 +37,8 @@ def test_params_default_and_validation():
     img = D.dibr_image(1, 640, 480, 1920, 1)
     assert D.dibr_validate(p, img) == D.DIBR_OK
     bad = [("depth_rule", 3), ("disparity_rule", 2), ("warp_mode", 2), ("max_parallax_px", -1),
-           ("max_parallax_px", 1025), ("threshold", 256), ("outputs", 0), ("outputs", 64)]
+           ("max_parallax_px", 1025), ("threshold", 256), ("outputs", 0), ("outputs", 64),
+           ("hole_fill", 2), ("hole_fill", -1)]
     for field, val in bad:
         q = D.dibr_params()
         D.dibr_params_default(q)
@@ -55,6 +56,14 @@ def test_params_default_and_validation():
     hs = D.make_params(outputs=("hsbs",))
     assert D.dibr_validate(hs, D.dibr_image(1, 5, 4, 15, 1)) == D.DIBR_E_INVALID
     assert D.dibr_validate(hs, D.dibr_image(1, 6, 4, 18, 1)) == D.DIBR_OK
+    # the 2-D fill: block side 1..32, even with HSBS; the holes map is a valid output
+    assert (p.hole_fill, p.inpaint_block) == (D.DIBR_FILL_ROW, 32)
+    for blk, ok in ((0, False), (1, True), (32, True), (33, False)):
+        q = D.make_params(hole_fill=D.DIBR_FILL_INPAINT2D, inpaint_block=blk)
+        assert (D.dibr_validate(q) == D.DIBR_OK) == ok, blk
+    assert D.dibr_validate(D.make_params(hole_fill=1, inpaint_block=7, outputs=("hsbs",))) == D.DIBR_E_INVALID
+    assert D.dibr_validate(D.make_params(hole_fill=1, inpaint_block=8, outputs=("hsbs",))) == D.DIBR_OK
+    assert D.dibr_validate(D.make_params(inpaint_block=0, outputs=("holes",))) == D.DIBR_OK  # unused with the row fill
 
 
 @pytest.mark.parametrize("rule", [0, 1])
