@@ -288,6 +288,44 @@ def bench_inpaint(D, torch, ctx, stream, reps=200):
             "launches_per_frame": 2}
 
 
+def bench_xbf(D, torch, ctx, stream, reps=200):
+    """4K L + R + anaglyph, P = 64, with the cross-bilateral depth (radius 2, sigma_s 1.5,
+    sigma_r 16) against the binomial depth on the same rotating buffer sets.  The
+    cross-bilateral kernel is bound by the SMs' exp2 rate: 25 exp2 per interior pixel."""
+    from paper_2009_09501_gb300 import scenes
+    img = torch.from_numpy(scenes.config_scene(2)).cuda()
+    H, W = img.shape[:2]
+    sets = [(img.clone(), {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS})
+            for _ in range(4)]
+    res = {}
+    for name, rule in (("binom5", D.DIBR_DEPTH_LUMA_BINOM5), ("xbf", D.DIBR_DEPTH_LUMA_XBF)):
+        p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, depth_rule=rule)
+        for k in range(10):
+            ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        e1.record(stream)
+        ctx.synchronize()
+        res[name] = e0.elapsed_time(e1) / reps * 1000.0
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    taps = sum(min(y + 2, H - 1) - max(y - 2, 0) + 1 for y in range(H)) * \
+        sum(min(x + 2, W - 1) - max(x - 2, 0) + 1 for x in range(W))
+    xbf_us = res["xbf"] - res["binom5"] + 0.0
+    clock_hz = 2.07e9  # the maximum SM clock; the clocks sampled in the timed region bound it
+    peak = 16 * props.multi_processor_count * clock_hz  # exp2 results per second (16 per SM per clock)
+    return {"workload": "3840x2160, P=64, L+R+anaglyph, cross-bilateral depth r=2",
+            "frames_per_s": 1e6 / res["xbf"], "us_per_frame": res["xbf"],
+            "binom5_us_per_frame": res["binom5"], "xbf_kernel_us_est": xbf_us,
+            "roofline": {"bound": "alu", "unit": "exp2/s", "exp2_per_frame": taps,
+                         "achieved": taps / (xbf_us * 1e-6) if xbf_us > 0 else None, "peak": peak,
+                         "frac": taps / (xbf_us * 1e-6) / peak if xbf_us > 0 else None,
+                         "peak_source": "16 exp2/clock/SM x SMs x 2.07 GHz (derived)",
+                         "note": "kernel time estimated as the frame time with this depth rule minus the binomial one"}}
+
+
 def bench_video(D, torch, ctx, frames=300):
     """4K video streamed from pinned host memory through one serving stream (H2D, kernel
     and D2H overlapped across frames), anaglyph, P = 64."""
@@ -467,6 +505,7 @@ def run_ours(args):
     if world == 1 and not args.quick:
         extra["batch"] = bench_batch(D, torch, ctx, stream)
         extra["inpaint2d"] = bench_inpaint(D, torch, ctx, stream)
+        extra["xbf"] = bench_xbf(D, torch, ctx, stream)
         extra["video"] = bench_video(D, torch, ctx)
         extra["served"] = bench_served(D, torch, args.served_seconds)
     if rank == 0:

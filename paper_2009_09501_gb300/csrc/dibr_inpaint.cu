@@ -26,7 +26,9 @@ namespace {
 
 constexpr int kMaxBlock = 32;
 constexpr int kStride = kMaxBlock + 2;  // cells per row of a block's colour frame
-constexpr int kBlocksPerCta = 4;        // image blocks per CTA; one warp per block and view
+constexpr int kBlocksPerCta = 1;        // image blocks per CTA; one warp per block and view
+// (one block per CTA: a heavily damaged block holds only its own two warps' slot, not the
+// slots of lighter blocks that finished long before it)
 
 // floor(v / (2n)) for v < 4096 and n = 2..8 as (v * ceil(65536 / 2n)) >> 16 (exact over that
 // range); index n.
@@ -51,8 +53,23 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
   const int B = a.block, W = a.W, H = a.H;
   int bx0 = 0, by0 = 0, bw = 0, bh = 0;
   if (blk < a.nblocks) {
-    bx0 = (blk % a.nbx) * B;
-    by0 = (blk / a.nbx) * B;
+    // the blocks of the first and last block columns go first: the whole background moves
+    // there, so their holes are the widest (up to P/2 columns) and they take longest
+    const int nbx = a.nbx, nby = a.nblocks / a.nbx;
+    int bx, by;
+    if (nbx <= 2) {
+      bx = blk % nbx;
+      by = blk / nbx;
+    } else if (blk < 2 * nby) {
+      bx = (blk & 1) ? nbx - 1 : 0;
+      by = blk >> 1;
+    } else {
+      const int i = blk - 2 * nby;
+      bx = 1 + i % (nbx - 2);
+      by = i / (nbx - 2);
+    }
+    bx0 = bx * B;
+    by0 = by * B;
     bw = min(B, W - bx0);
     bh = min(B, H - by0);
   }
@@ -125,89 +142,118 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
     __syncwarp();
 
     const uint64_t rows = ((1ull << bh) - 1ull) << 1;  // the block's own rows in a column mask
-    // A damaged pixel whose neighbourhood has not changed since it last failed the test
-    // fails it again, so a visit only checks "dirty" pixels: all of them in the first pass,
-    // then those next to a pixel repaired since their last check.  The result is the same
-    // as checking every damaged pixel; the work follows the repair front.
-    uint64_t dirty = lane < bw ? own & rows : 0ull;
-    uint64_t lm = __shfl_up_sync(0xffffffffu, own, 1);
-    uint64_t rm = __shfl_down_sync(0xffffffffu, own, 1);
-    if (lane == 0) lm = halo_l;
-    if (lane == bw - 1) rm = halo_r;
-    // the steps at which some lane visits a dirty damaged pixel: lane x visits block row r
-    // at step 2x + r (steps 0..93, three words)
-    auto active = [&](uint32_t (&act)[3]) {
-      const uint64_t dm = lane < bw ? (own & dirty & rows) >> 1 : 0ull;
+    uint64_t lm = 0, rm = 0;  // damage flags of the neighbouring columns
+    auto refresh = [&]() {
+      lm = __shfl_up_sync(0xffffffffu, own, 1);
+      rm = __shfl_down_sync(0xffffffffu, own, 1);
+      if (lane == 0) lm = halo_l;
+      if (lane == bw - 1) rm = halo_r;
+    };
+    // The visit of damaged block row r of this lane's column: with two or more undamaged
+    // neighbours the pixel takes their mean colour and is no longer damaged.
+    auto visit = [&](int r) -> bool {
+      // frame rows r, r + 1 (the pixel's own), r + 2 of the three columns
+      const uint32_t bl = static_cast<uint32_t>(lm >> r) & 7u;
+      const uint32_t bo = static_cast<uint32_t>(own >> r) & 5u;
+      const uint32_t br = static_cast<uint32_t>(rm >> r) & 7u;
+      const int n = 8 - __popc(bl) - __popc(bo) - __popc(br);
+      if (n < 2) return false;
+      uint32_t srb = 0, sg = 0;  // red and blue sums in two 16-bit lanes, green alone
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj) {
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+          const uint32_t m = di == 0 ? bl : di == 1 ? bo : br;
+          if (di == 1 && dj == 1) continue;
+          if ((m >> dj) & 1u) continue;
+          const uint32_t c = cell[(r + dj) * kStride + lane + di];
+          srb += c & 0x00FF00FFu;
+          sg += __byte_perm(c, 0u, 0x4441u);
+        }
+      }
+      // per channel floor((2 sum + n) / 2n): the mean rounded half up
+      const uint32_t rc = kHalfRecip[n];
+      const uint32_t mr = ((2u * (srb & 0xFFFFu) + n) * rc) >> 16, mb = ((2u * (srb >> 16) + n) * rc) >> 16;
+      const uint32_t mg = ((2u * sg + n) * rc) >> 16;
+      cell[(r + 1) * kStride + lane + 1] = mr | (mg << 8) | (mb << 16);
+      own &= ~(1ull << (r + 1));
+      return true;
+    };
+    // the steps at which some lane visits a pixel of mask bits `sel`: lane x visits block
+    // row r at step 2x + r (steps 0..93, three words)
+    auto steps_of = [&](uint64_t sel, uint32_t (&act)[3]) {
+      const uint64_t dm = lane < bw ? (sel & rows) >> 1 : 0ull;
       const int sh = 2 * lane;
       const uint64_t lo = dm << sh, hi = sh ? dm >> (64 - sh) : 0ull;
       act[0] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo));
       act[1] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo >> 32));
       act[2] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(hi));
     };
-    // passes over the block in the visiting order, while a pass repairs something
-    while (true) {
+
+    // ---- first pass: every damaged pixel is visited
+    uint64_t rep1 = 0;
+    {
       uint32_t act[3];
-      active(act);
-      bool fixed = false;
+      steps_of(own, act);
       for (int w = 0; w < 3; ++w) {
         while (act[w]) {
           const int s = 32 * w + __ffs(act[w]) - 1;
           act[w] &= act[w] - 1;
+          refresh();
           const int r = s - 2 * lane;  // block row this lane visits at step s
-          const bool cand = lane < bw && r >= 0 && r < bh && ((own & dirty) >> (r + 1)) & 1ull;
-          bool rep = false;
-          if (cand) {
-            dirty &= ~(1ull << (r + 1));
-            // frame rows r, r + 1 (the pixel's own), r + 2 of the three columns
-            const uint32_t bl = static_cast<uint32_t>(lm >> r) & 7u;
-            const uint32_t bo = static_cast<uint32_t>(own >> r) & 5u;
-            const uint32_t br = static_cast<uint32_t>(rm >> r) & 7u;
-            const int n = 8 - __popc(bl) - __popc(bo) - __popc(br);
-            if (n >= 2) {
-              uint32_t sr = 0, sg = 0, sb = 0;
-#pragma unroll
-              for (int dj = 0; dj < 3; ++dj) {
-#pragma unroll
-                for (int di = 0; di < 3; ++di) {
-                  const uint32_t m = di == 0 ? bl : di == 1 ? bo : br;
-                  if (di == 1 && dj == 1) continue;
-                  if ((m >> dj) & 1u) continue;
-                  const uint32_t c = cell[(r + dj) * kStride + lane + di];
-                  sr += c & 0xFFu;
-                  sg += (c >> 8) & 0xFFu;
-                  sb += c >> 16;
-                }
-              }
-              // per channel floor((2 sum + n) / 2n): the mean rounded half up
-              const uint32_t rc = kHalfRecip[n];
-              const uint32_t c = (((2u * sr + n) * rc) >> 16) | ((((2u * sg + n) * rc) >> 16) << 8) |
-                                 ((((2u * sb + n) * rc) >> 16) << 16);
-              cell[(r + 1) * kStride + lane + 1] = c;
-              own &= ~(1ull << (r + 1));
-              rep = true;
-            }
-          }
+          if (static_cast<unsigned>(r) < static_cast<unsigned>(bh) && lane < bw && ((own >> (r + 1)) & 1ull) &&
+              visit(r))
+            rep1 |= 1ull << (r + 1);
           __syncwarp();
-          if (__any_sync(0xffffffffu, rep)) {
-            // new neighbour columns; their damaged neighbours (and this column's) become dirty
-            uint64_t nl = __shfl_up_sync(0xffffffffu, own, 1);
-            uint64_t nr = __shfl_down_sync(0xffffffffu, own, 1);
-            if (lane == 0) nl = halo_l;
-            if (lane == bw - 1) nr = halo_r;
-            const uint64_t gone = (lm & ~nl) | (rm & ~nr) | (rep ? 1ull << (r + 1) : 0ull);
-            lm = nl;
-            rm = nr;
-            dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
-            fixed = true;
-            // a repair at step s can make pixels later in this pass dirty only at steps
-            // s + 1 (the next row of its column) .. s + 3 (the next column's three rows)
-            if (s + 1 < 96) act[(s + 1) >> 5] |= 1u << ((s + 1) & 31);
-            if (s + 2 < 96) act[(s + 2) >> 5] |= 1u << ((s + 2) & 31);
-            if (s + 3 < 96) act[(s + 3) >> 5] |= 1u << ((s + 3) & 31);
-          }
         }
       }
-      if (!fixed || !__any_sync(0xffffffffu, lane < bw && (own & rows) != 0)) break;
+    }
+    // ---- later passes, while one repairs something.  A damaged pixel whose neighbourhood
+    // has not changed since it last failed the test fails it again, so a visit only checks
+    // "dirty" pixels: those next to a pixel repaired since their last check (after the
+    // first pass: next to any pixel it repaired).  The result is the same as visiting
+    // every damaged pixel; the work follows the repair front.
+    bool more = __any_sync(0xffffffffu, rep1 != 0) && __any_sync(0xffffffffu, lane < bw && (own & rows) != 0);
+    if (more) {
+      const uint64_t rl = __shfl_up_sync(0xffffffffu, rep1, 1), rr = __shfl_down_sync(0xffffffffu, rep1, 1);
+      const uint64_t near = rep1 | (lane > 0 ? rl : 0ull) | (lane < bw - 1 ? rr : 0ull);
+      uint64_t dirty = (near | (near << 1) | (near >> 1)) & own & rows;
+      refresh();
+      while (more) {
+        uint32_t act[3];
+        steps_of(own & dirty, act);
+        bool fixed = false;
+        for (int w = 0; w < 3; ++w) {
+          while (act[w]) {
+            const int s = 32 * w + __ffs(act[w]) - 1;
+            act[w] &= act[w] - 1;
+            const int r = s - 2 * lane;
+            const bool cand = static_cast<unsigned>(r) < static_cast<unsigned>(bh) && lane < bw &&
+                              (((own & dirty) >> (r + 1)) & 1ull);
+            bool rep = false;
+            if (cand) {
+              dirty &= ~(1ull << (r + 1));
+              rep = visit(r);
+            }
+            __syncwarp();
+            if (__any_sync(0xffffffffu, rep)) {
+              // new neighbour columns; their damaged neighbours (and this column's) become dirty
+              const uint64_t ol = lm, orr = rm;
+              refresh();
+              const uint64_t gone = (ol & ~lm) | (orr & ~rm) | (rep ? 1ull << (r + 1) : 0ull);
+              dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
+              fixed = true;
+              // a repair at step s can make pixels later in this pass dirty only at steps
+              // s + 1 (the next row of its column) .. s + 3 (the next column's three rows);
+              // those steps are visited (a step with no dirty damaged pixel does nothing)
+#pragma unroll
+              for (int k = 1; k <= 3; ++k)
+                if (s + k < 96) act[(s + k) >> 5] |= 1u << ((s + k) & 31);
+            }
+          }
+        }
+        more = fixed && __any_sync(0xffffffffu, lane < bw && (own & rows) != 0);
+      }
     }
     // ---- repaired pixels back into the view
     const uint64_t rep = lane < bw ? (own0 & ~own & rows) : 0ull;

@@ -3,82 +3,124 @@
 //
 // Guide = the RGB image.  For pixel p the window is the square |dx|,|dy| <= r clipped to
 // the image; sample q has weight exp(-(dx^2+dy^2)/(2 s_s^2) - |RGB(p)-RGB(q)|^2/(2 s_r^2))
-// and D(p) = round-half-up(sum w Y(q) / sum w).  FP32 with expf; the sums are taken
-// relative to Y(p) (sum w (Y(q) - Y(p))), which is the same quotient and keeps the
-// rounding error of the accumulation small next to the final half-integer decision.
+// and D(p) = round-half-up(sum w Y(q) / sum w).  FP32; the sums are taken relative to
+// Y(p) (sum w (Y(q) - Y(p))), which is the same quotient and keeps the rounding error of
+// the accumulation small next to the final half-integer decision.
 //
-// One CTA computes a 32 x 8 tile; the tile plus an r-pixel apron of colours and
-// luminances is staged in shared memory once, then every thread runs its (2r+1)^2 taps.
+// One CTA computes a 32 x 8 tile; the tile plus an r-pixel apron is staged in shared
+// memory once, one word per pixel: RGB in the low three bytes, the luminance in the top
+// byte.  Per tap: one shared load, the squared colour distance exactly in two integer
+// instructions (per-byte absolute differences, then a byte dot product of that word
+// with itself, the luminance byte masked out), one FMA for the exponent (the spatial
+// part is a per-tap constant: the radius is a template parameter, so the taps unroll),
+// one exp2 on the special-function unit (the constants are pre-scaled by log2 e), and
+// two accumulations.  Integer-to-float conversions, which share the special-function
+// unit's low rate, are replaced by exact mantissa tricks, so the exp2 is the only such
+// operation per tap.
 #include "dibr_internal.h"
 
 namespace dibr {
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kMaxR = 8;
-constexpr int kAX = kTX + 2 * kMaxR, kAY = kTY + 2 * kMaxR;
+constexpr int kTX = 32, kTY = 8;  // tile; radius 1..8 (template parameter)
 
 __device__ __forceinline__ uint32_t luma8x(uint32_t r, uint32_t g, uint32_t b) {
   return (299u * r + 587u * g + 114u * b + 500u) / 1000u;
 }
 
-__global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch,
-                                                       int W, int H, int R, float as, float ar,
-                                                       uint8_t *__restrict__ D, int64_t dpitch) {
-  __shared__ uint32_t col[kAY][kAX];  // 0x00BBGGRR, bit 31 set outside the image
-  __shared__ float lum[kAY][kAX];
+// 2^x on the special-function unit (results below 2^-126 flush to zero).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Integers below 2^23 become floats without the conversion unit: OR-ed into the mantissa of
+// 2^23 (bit pattern 0x4B000000), minus 2^23, exactly.
+constexpr float kTwo23 = 8388608.0f;
+
+// One tap: q's packed word cq against the centre's cp.  es = -(dx^2+dy^2) as log2(e);
+// ypo = 2^23 + Y(p).
+__device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float es, float nar, float ypo, float &num,
+                                        float &den) {
+  const uint32_t v = __vabsdiffu4(cp, cq);
+  const uint32_t d2 = __dp4a(v & 0x00FFFFFFu, v, 0u);  // |RGB(p) - RGB(q)|^2, exact, < 2^18
+  const float fd2 = __uint_as_float(0x4B000000u | d2) - kTwo23;
+  const float w = ex2(fmaf(fd2, nar, es));
+  const float dy = __uint_as_float(__byte_perm(cq, 0x4B000000u, 0x7543)) - ypo;  // Y(q) - Y(p), exact
+  num = fmaf(w, dy, num);
+  den += w;
+}
+
+template <int R>
+__global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
+                                                       float as, float ar, uint8_t *__restrict__ D, int64_t dpitch) {
+  __shared__ uint32_t px[kTY + 2 * R][kTX + 2 * R];  // 0xYYBBGGRR
   const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY;
-  const int ax = kTX + 2 * R, ay = kTY + 2 * R;
+  constexpr int ax = kTX + 2 * R, ay = kTY + 2 * R;
   for (int i = threadIdx.x; i < ax * ay; i += blockDim.x) {
     const int ty = i / ax, tx = i - ty * ax;
     const int gx = bx - R + tx, gy = by - R + ty;
-    uint32_t c = 0x80000000u;
-    float l = 0.f;
+    uint32_t c = 0u;  // outside the image: never read (the window is clipped)
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       const uint8_t *p = rgb + static_cast<int64_t>(gy) * pitch + 3 * static_cast<int64_t>(gx);
       const uint32_t r = p[0], g = p[1], b = p[2];
-      c = r | (g << 8) | (b << 16);
-      l = static_cast<float>(luma8x(r, g, b));
+      c = r | (g << 8) | (b << 16) | (luma8x(r, g, b) << 24);
     }
-    col[ty][tx] = c;
-    lum[ty][tx] = l;
+    px[ty][tx] = c;
   }
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const int x = bx + tx, y = by + ty;
   if (x >= W || y >= H) return;
-  const uint32_t cp = col[ty + R][tx + R];
-  const float yp = lum[ty + R][tx + R];
-  const int pr = cp & 255, pg = (cp >> 8) & 255, pb = (cp >> 16) & 255;
+  const uint32_t cp = px[ty + R][tx + R];
+  const float ypo = kTwo23 + static_cast<float>(cp >> 24);
+  // exponents in base 2: w = 2^(-(s2 * as + d2 * ar) * log2 e)
+  constexpr float kLog2e = 1.4426950408889634f;
+  const float nas = -as * kLog2e, nar = -ar * kLog2e;
   float num = 0.f, den = 0.f;
-  for (int dy = -R; dy <= R; ++dy) {
-    for (int dx = -R; dx <= R; ++dx) {
-      const uint32_t cq = col[ty + R + dy][tx + R + dx];
-      if (cq & 0x80000000u) continue;
-      const int er = pr - static_cast<int>(cq & 255), eg = pg - static_cast<int>((cq >> 8) & 255),
-                eb = pb - static_cast<int>((cq >> 16) & 255);
-      const float d2 = static_cast<float>(er * er + eg * eg + eb * eb);
-      const float s2 = static_cast<float>(dx * dx + dy * dy);
-      const float w = expf(-fmaf(s2, as, d2 * ar));
-      num = fmaf(w, lum[ty + R + dy][tx + R + dx] - yp, num);
-      den += w;
-    }
+  if (x >= R && x + R < W && y >= R && y + R < H) {
+#pragma unroll
+    for (int dy = -R; dy <= R; ++dy)
+#pragma unroll
+      for (int dx = -R; dx <= R; ++dx)
+        xbf_tap(cp, px[ty + R + dy][tx + R + dx], static_cast<float>(dx * dx + dy * dy) * nas, nar, ypo, num, den);
+  } else {  // the window clipped to the image
+    const int x0 = max(-R, -x), x1 = min(R, W - 1 - x), y0 = max(-R, -y), y1 = min(R, H - 1 - y);
+    for (int dy = y0; dy <= y1; ++dy)
+      for (int dx = x0; dx <= x1; ++dx)
+        xbf_tap(cp, px[ty + R + dy][tx + R + dx], static_cast<float>(dx * dx + dy * dy) * nas, nar, ypo, num, den);
   }
   const float q = floorf(num / den + 0.5f);
-  const int v = static_cast<int>(yp) + static_cast<int>(q);
+  const int v = static_cast<int>(cp >> 24) + static_cast<int>(q);
   D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
+}
+
+template <int R>
+cudaError_t launch_r(const uint8_t *rgb, int64_t pitch, int W, int H, float as, float ar, uint8_t *D, int64_t dpitch,
+                     cudaStream_t st) {
+  dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+  xbf_kernel<R><<<grid, kTX * kTY, 0, st>>>(rgb, pitch, W, H, as, ar, D, dpitch);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius, float sigma_s,
                        float sigma_r, uint8_t *D, int64_t dpitch, cudaStream_t st) {
-  if (radius < 1 || radius > kMaxR) return cudaErrorInvalidValue;
-  const double as = 1.0 / (2.0 * static_cast<double>(sigma_s) * sigma_s);
-  const double ar = 1.0 / (2.0 * static_cast<double>(sigma_r) * sigma_r);
-  dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
-  xbf_kernel<<<grid, kTX * kTY, 0, st>>>(rgb, pitch, W, H, radius, static_cast<float>(as),
-                                         static_cast<float>(ar), D, dpitch);
-  return cudaGetLastError();
+  const float as = static_cast<float>(1.0 / (2.0 * static_cast<double>(sigma_s) * sigma_s));
+  const float ar = static_cast<float>(1.0 / (2.0 * static_cast<double>(sigma_r) * sigma_r));
+  switch (radius) {
+    case 1: return launch_r<1>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 2: return launch_r<2>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 3: return launch_r<3>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 4: return launch_r<4>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 5: return launch_r<5>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 6: return launch_r<6>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 7: return launch_r<7>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 8: return launch_r<8>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace dibr

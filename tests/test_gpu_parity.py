@@ -178,7 +178,18 @@ def test_xbf_depth_tolerance_and_exact_back_half(ctx, torch, oracle):
     assert_same({k: got[k] for k in ALL[:4]}, back, "xbf back half")
 
 
-@pytest.mark.parametrize("radius,ss,sr", [(1, 0.8, 8.0), (3, 2.0, 24.0), (8, 4.0, 50.0)])
+def test_xbf_4k_depth_tolerance(ctx, torch, oracle):
+    img = scenes.config_scene(2)
+    kw = dict(max_parallax=64, depth_rule=2)
+    got = run_device(ctx, torch, img, ("depth",), **kw)["depth"]
+    refD = oracle.depth(img, oracle_params(oracle, **kw))
+    diff = np.abs(got.astype(int) - refD.astype(int))
+    assert diff.max() <= 1
+    assert (diff > 0).mean() <= 1e-4, (diff > 0).mean()
+
+
+@pytest.mark.parametrize("radius,ss,sr", [(1, 0.8, 8.0), (2, 1.5, 16.0), (3, 2.0, 24.0), (5, 3.0, 30.0),
+                                          (8, 4.0, 50.0)])
 def test_xbf_parameters(ctx, torch, oracle, radius, ss, sr):
     img = scenes.Scene(300, 120, seed=31, texture="gauss8").frame(0)
     kw = dict(max_parallax=16, depth_rule=2, xbf_radius=radius, xbf_sigma_s=ss, xbf_sigma_r=sr)
