@@ -704,6 +704,9 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 // ---------------------------------------------------------------------------------
 // One image: CTA b owns the rows [b*H/grid, (b+1)*H/grid).
 __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
+  // The next launch on the stream may start its set-up while this one runs (programmatic
+  // dependent launch); it waits below for this one to complete before any global access.
+  griddep_launch_dependents();
   extern __shared__ __align__(128) uint8_t smem[];
   const Shm m = carve(smem, a.nb, a.srow, a.nch, a.depth_src);
   fill_luts(m, a.lut_h, a.lut_n, a.warp_mode == DIBR_WARP_FORWARD);
@@ -712,6 +715,9 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
     fence_mbar_init();
   }
   __syncthreads();
+  // the work before this launch on the stream (whose results may be this launch's inputs,
+  // or whose inputs this launch's outputs may overwrite) has completed
+  griddep_wait();
   const int ys = static_cast<int>(static_cast<int64_t>(blockIdx.x) * a.H / a.grid);
   const int ye = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * a.H / a.grid);
   if (ys >= ye) return;
@@ -794,8 +800,18 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
   static bool done = false;  // per process: the attribute is per function
   cudaError_t e = allow_smem(band_kernel, done);
   if (e != cudaSuccess) return e;
-  band_kernel<<<a.grid, a.nc, smem_bytes, st>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.grid);
+  cfg.blockDim = dim3(a.nc);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, band_kernel, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {

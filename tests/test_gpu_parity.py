@@ -226,3 +226,19 @@ def test_batch_equals_single(ctx, torch):
     ctx.synthesize_batch(imgs, params, outs)
     for o, s in zip(outs, singles):
         assert np.array_equal(o["anaglyph"].cpu().numpy(), s)
+
+
+def test_page_locked_host_outputs(ctx, torch, oracle):
+    # outputs in page-locked host memory, both fills
+    img = scenes.Scene(640, 360, seed=77, n_objects=10).frame(0)
+    H, W, _ = img.shape
+    want = ("anaglyph", "left", "right", "hsbs", "depth", "holes")
+    outs = {n: torch.zeros((H, W) if n in D.MAP_OUTPUTS else (H, W, 3), dtype=torch.uint8).pin_memory()
+            for n in want}
+    for fill in (0, 1):
+        p = D.make_params(max_parallax=24, outputs=want, hole_fill=fill, inpaint_block=16)
+        for v in outs.values():
+            v.fill_(3)
+        ctx.synthesize_image(np.ascontiguousarray(img), p, {n: v.numpy() for n, v in outs.items()})
+        ref = oracle.dibr(img, oracle.params(max_parallax=24, fill_mode=fill, inpaint_block=16), want=want)
+        assert_same({n: v.numpy() for n, v in outs.items()}, ref, "pinned host fill=%d" % fill)
