@@ -8,15 +8,15 @@
 // the accumulation small next to the final half-integer decision.
 //
 // One CTA computes a 32 x 8 tile; the tile plus an r-pixel apron is staged in shared
-// memory once, one word per pixel: RGB in the low three bytes, the luminance in the top
-// byte.  Per tap: one shared load, the squared colour distance exactly in two integer
+// memory once: the colour (RGB in the low three bytes) and the luminance (as a float).
+// Per tap: two shared loads, the squared colour distance exactly in two integer
 // instructions (per-byte absolute differences, then a byte dot product of that word
-// with itself, the luminance byte masked out), one FMA for the exponent (the spatial
+// with itself), one FMA for the exponent (the spatial
 // part is a per-tap constant: the radius is a template parameter, so the taps unroll),
 // one exp2 on the special-function unit (the constants are pre-scaled by log2 e), and
-// two accumulations.  Integer-to-float conversions, which share the special-function
-// unit's low rate, are replaced by exact mantissa tricks, so the exp2 is the only such
-// operation per tap.
+// two accumulations.  The integer-to-float conversion of the distance, which would share
+// the special-function unit's low rate, is an exact mantissa trick, so the exp2 is the
+// only such operation per tap.
 #include "dibr_internal.h"
 
 namespace dibr {
@@ -39,42 +39,45 @@ __device__ __forceinline__ float ex2(float x) {
 // 2^23 (bit pattern 0x4B000000), minus 2^23, exactly.
 constexpr float kTwo23 = 8388608.0f;
 
-// One tap: q's packed word cq against the centre's cp.  es = -(dx^2+dy^2) as log2(e);
-// ypo = 2^23 + Y(p).
-__device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float es, float nar, float ypo, float &num,
+// One tap: q's colour cq and luminance yq against the centre's colour cp and luminance yp;
+// es = -(dx^2+dy^2) as log2(e).
+__device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float yq, float es, float nar, float yp, float &num,
                                         float &den) {
   const uint32_t v = __vabsdiffu4(cp, cq);
-  const uint32_t d2 = __dp4a(v & 0x00FFFFFFu, v, 0u);  // |RGB(p) - RGB(q)|^2, exact, < 2^18
+  const uint32_t d2 = __dp4a(v, v, 0u);  // |RGB(p) - RGB(q)|^2, exact, < 2^18
   const float fd2 = __uint_as_float(0x4B000000u | d2) - kTwo23;
   const float w = ex2(fmaf(fd2, nar, es));
-  const float dy = __uint_as_float(__byte_perm(cq, 0x4B000000u, 0x7543)) - ypo;  // Y(q) - Y(p), exact
-  num = fmaf(w, dy, num);
+  num = fmaf(w, yq - yp, num);
   den += w;
 }
 
 template <int R>
 __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
                                                        float as, float ar, uint8_t *__restrict__ D, int64_t dpitch) {
-  __shared__ uint32_t px[kTY + 2 * R][kTX + 2 * R];  // 0xYYBBGGRR
+  __shared__ uint32_t col[kTY + 2 * R][kTX + 2 * R];  // 0x00BBGGRR
+  __shared__ float lum[kTY + 2 * R][kTX + 2 * R];
   const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY;
   constexpr int ax = kTX + 2 * R, ay = kTY + 2 * R;
   for (int i = threadIdx.x; i < ax * ay; i += blockDim.x) {
     const int ty = i / ax, tx = i - ty * ax;
     const int gx = bx - R + tx, gy = by - R + ty;
     uint32_t c = 0u;  // outside the image: never read (the window is clipped)
+    uint32_t l = 0u;
     if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
       const uint8_t *p = rgb + static_cast<int64_t>(gy) * pitch + 3 * static_cast<int64_t>(gx);
       const uint32_t r = p[0], g = p[1], b = p[2];
-      c = r | (g << 8) | (b << 16) | (luma8x(r, g, b) << 24);
+      c = r | (g << 8) | (b << 16);
+      l = luma8x(r, g, b);
     }
-    px[ty][tx] = c;
+    col[ty][tx] = c;
+    lum[ty][tx] = static_cast<float>(l);
   }
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const int x = bx + tx, y = by + ty;
   if (x >= W || y >= H) return;
-  const uint32_t cp = px[ty + R][tx + R];
-  const float ypo = kTwo23 + static_cast<float>(cp >> 24);
+  const uint32_t cp = col[ty + R][tx + R];
+  const float yp = lum[ty + R][tx + R];
   // exponents in base 2: w = 2^(-(s2 * as + d2 * ar) * log2 e)
   constexpr float kLog2e = 1.4426950408889634f;
   const float nas = -as * kLog2e, nar = -ar * kLog2e;
@@ -84,15 +87,17 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
     for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx)
-        xbf_tap(cp, px[ty + R + dy][tx + R + dx], static_cast<float>(dx * dx + dy * dy) * nas, nar, ypo, num, den);
+        xbf_tap(cp, col[ty + R + dy][tx + R + dx], lum[ty + R + dy][tx + R + dx],
+                static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
   } else {  // the window clipped to the image
     const int x0 = max(-R, -x), x1 = min(R, W - 1 - x), y0 = max(-R, -y), y1 = min(R, H - 1 - y);
     for (int dy = y0; dy <= y1; ++dy)
       for (int dx = x0; dx <= x1; ++dx)
-        xbf_tap(cp, px[ty + R + dy][tx + R + dx], static_cast<float>(dx * dx + dy * dy) * nas, nar, ypo, num, den);
+        xbf_tap(cp, col[ty + R + dy][tx + R + dx], lum[ty + R + dy][tx + R + dx],
+                static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
   }
   const float q = floorf(num / den + 0.5f);
-  const int v = static_cast<int>(cp >> 24) + static_cast<int>(q);
+  const int v = static_cast<int>(yp) + static_cast<int>(q);
   D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
 }
 
