@@ -244,7 +244,9 @@ dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const di
  *                  mode 5, which fits every image;
  *   l2_prefetch    1: each CTA prefetches its later input rows into L2 at launch;
  *                  2: it does not;
- *   rows_per_unit  rows per work unit of a batched launch (dibr_synthesize_batch).
+ *   rows_per_unit  rows per work unit of a batched launch (dibr_synthesize_batch and
+ *                  the serving loop); automatic: one unit per SM slot when an image group
+ *                  is small (one 4K frame: 8 rows), 32 rows otherwise.
  * dibr_set_tuning() rejects out-of-range values with DIBR_E_INVALID. */
 typedef struct {
     int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit;

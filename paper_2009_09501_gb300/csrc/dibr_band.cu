@@ -742,6 +742,10 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
 // A batch of images in one persistent launch: CTAs pull work units (an image and a
 // range of its rows) from a device counter until none is left.
 __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
+  // The next launch of the batch (another group of images, independent of this one) may be
+  // placed as soon as every CTA of this one runs: its CTAs take the SM slots this launch
+  // frees while its last units finish, instead of waiting for the last of them.
+  griddep_launch_dependents();
   extern __shared__ __align__(128) uint8_t smem[];
   int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, DS_BINOM5).flags);
   const Shm m = carve(smem, b.nb, b.srow, b.nch_max, DS_BINOM5);
@@ -775,11 +779,8 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     __syncthreads();
     if (!run_band(j, m, un.y, un.z, kbase, b.status, b.timeout_ns)) break;
   }
-  // No unit is left for this CTA: the next launch of the batch (another group of images,
-  // independent of this one) may start filling the SMs this launch leaves.  A chained
-  // launch's CTAs then wait for the previous launch to complete before they exit, so that
-  // the work after the batch in stream order still follows all of it.
-  griddep_launch_dependents();
+  // A chained launch's CTAs wait for the previous launch to complete before they exit, so
+  // that the work after the batch in stream order still follows all of it.
   griddep_wait();
 }
 

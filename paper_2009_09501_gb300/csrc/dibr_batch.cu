@@ -1,7 +1,7 @@
 // dibr_batch.cu -- images of uneven sizes in one persistent launch (dibr_synthesize_batch,
 // dibr_enqueue_batch).
 //
-// Each image is cut into work units of rows_per_unit rows.  The host writes one
+// Each image is cut into work units of a few rows (plan_unit_rows).  The host writes one
 // descriptor per image (pointers, sizes, shift tables) and the unit list, largest images
 // first, into device memory with a single copy; the persistent CTAs of the batch kernel
 // take units from a device counter until none is left, so the launch balances itself
@@ -46,7 +46,6 @@ void dibr_ctx::release_batch_buffers() {
 dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
                                            const dibr_outputs *outs) {
   if (n == 0) return DIBR_OK;
-  const int rows_per_unit = tuning.rows_per_unit > 0 ? tuning.rows_per_unit : 32;
   // --- inputs that a bulk row copy cannot read directly are repacked (16-byte rows)
   std::vector<const uint8_t *> in(n);
   std::vector<int64_t> in_pitch(n);
@@ -110,11 +109,12 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
     return DIBR_E_INVALID;
   }
   order_by_area(n, widths.data(), heights.data(), order.data());
+  plan_unit_rows(n, heights.data(), class_of.data(), nclass, num_sms, tuning.rows_per_unit, cls);
 
   // --- descriptors and units, staged in pinned memory; each group's units are
   // contiguous, largest images first
   int n_units = 0;
-  for (int i = 0; i < n; ++i) n_units += (imgs[i].height + rows_per_unit - 1) / rows_per_unit;
+  for (int i = 0; i < n; ++i) n_units += (imgs[i].height + cls[class_of[i]].rows - 1) / cls[class_of[i]].rows;
   // [counters][pad] [descs] [units]: every part 256-byte aligned (the kernel reads the
   // units as int4 and the descriptors' 64-bit fields)
   const size_t off_desc = 256;
@@ -166,8 +166,9 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
     for (int oi = 0; oi < n; ++oi) {
       const int i = order[oi];
       if (class_of[i] != c) continue;
-      for (int y0 = 0; y0 < imgs[i].height; y0 += rows_per_unit)
-        units[u++] = make_int4(i, y0, std::min(imgs[i].height, y0 + rows_per_unit), 0);
+      const int rpu = cls[c].rows;
+      for (int y0 = 0; y0 < imgs[i].height; y0 += rpu)
+        units[u++] = make_int4(i, y0, std::min(imgs[i].height, y0 + rpu), 0);
     }
     cls[c].n_units = u - cls[c].unit_begin;
   }

@@ -155,6 +155,7 @@ struct BatchClass {
   int srow;        // bytes per ring slot
   int nb, per;     // ring slots; CTAs per SM
   int smem;        // dynamic shared memory per block
+  int rows;        // rows per work unit
   int unit_begin, n_units;
 };
 
@@ -178,7 +179,7 @@ inline int plan_batch_classes(int n, const int *width, const int *row_bytes, con
     if (c == nclass || cls[c].nc != nc) {
       if (nclass == kMaxClasses) return -1;
       for (int k = nclass; k > c; --k) cls[k] = cls[k - 1];
-      cls[c] = BatchClass{nc, 1, 128, 4, 0, 0, 0, 0};
+      cls[c] = BatchClass{nc, 1, 128, 4, 0, 0, 0, 0, 0};
       ++nclass;
     }
   }
@@ -213,6 +214,29 @@ inline int plan_batch_classes(int n, const int *width, const int *row_bytes, con
     k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, DS_BINOM5).total;
   }
   return nclass;
+}
+
+// Rows per work unit of each group: a group whose rows fill the SM slots (sms x CTAs per
+// SM) at most kUnitRows deep gets one unit per slot -- e.g. one 4K frame: 2160 rows over 304
+// slots, 8 rows each -- so that every slot has work; a larger group gets kUnitRows-row units,
+// enough of them for the slots to stay balanced.  A fixed size (rows > 0) overrides.  Each
+// unit recomputes the two rows of context above it, so units are not made smaller than
+// needed.
+constexpr int kUnitRows = 32;
+inline void plan_unit_rows(int n, const int *height, const int *class_of, int nclass, int sms, int rows,
+                           BatchClass *cls) {
+  for (int c = 0; c < nclass; ++c) {
+    if (rows > 0) {
+      cls[c].rows = rows;
+      continue;
+    }
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i)
+      if (class_of[i] == c) total += height[i];
+    const int64_t slots = static_cast<int64_t>(sms) * (cls[c].per > 0 ? cls[c].per : 1);
+    cls[c].rows = total <= slots * kUnitRows ? static_cast<int>((total + slots - 1) / slots) : kUnitRows;
+    if (cls[c].rows < 1) cls[c].rows = 1;
+  }
 }
 
 // order[0..n) = image indices, largest area first (stable insertion sort, no allocation)

@@ -107,14 +107,6 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     heights[i] = imgs[i].height;
     row_bytes[i] = 3 * imgs[i].width;
   }
-  // work units of at least 32 rows, more when the unit list would not fit
-  int rows_per_unit = 32;
-  auto count_units = [&](int r) {
-    int64_t u = 0;
-    for (int i = 0; i < n; ++i) u += (imgs[i].height + r - 1) / r;
-    return u;
-  };
-  while (count_units(rows_per_unit) > kStaticMaxUnits) rows_per_unit *= 2;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) {
@@ -134,6 +126,15 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
   const int nclass = plan_batch_classes(n, widths, row_bytes, lim, class_of, cls);
   if (nclass < 1) return DIBR_E_INVALID;
   order_by_area(n, widths, heights, order);
+  // rows per unit as for the context's batches, larger while the unit list would not fit
+  plan_unit_rows(n, heights, class_of, nclass, d.sms, 0, cls);
+  auto count_units = [&]() {
+    int64_t u = 0;
+    for (int i = 0; i < n; ++i) u += (heights[i] + cls[class_of[i]].rows - 1) / cls[class_of[i]].rows;
+    return u;
+  };
+  while (count_units() > kStaticMaxUnits)
+    for (int c = 0; c < nclass; ++c) cls[c].rows *= 2;
 
   // descriptors and units into the host staging; the header zeroes the groups' unit
   // counters and the status word, which every call needs to start at zero
@@ -166,8 +167,9 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     for (int oi = 0; oi < n; ++oi) {
       const int i = order[oi];
       if (class_of[i] != c) continue;
-      for (int y0 = 0; y0 < imgs[i].height; y0 += rows_per_unit)
-        units[n_units++] = make_int4(i, y0, y0 + rows_per_unit < imgs[i].height ? y0 + rows_per_unit : imgs[i].height, 0);
+      const int rpu = cls[c].rows;
+      for (int y0 = 0; y0 < imgs[i].height; y0 += rpu)
+        units[n_units++] = make_int4(i, y0, y0 + rpu < imgs[i].height ? y0 + rpu : imgs[i].height, 0);
     }
     cls[c].n_units = n_units - cls[c].unit_begin;
   }
