@@ -160,6 +160,11 @@ __device__ __forceinline__ uint4 binom_h(const uint32_t (&V)[10]) {
   return make_uint4(d[0], d[1], d[2], d[3]);
 }
 
+// Target offsets of a source from its packed table entry: -hL (low half) and -hR (high
+// half), both sign-extended.
+__device__ __forceinline__ int shift_l(uint32_t w) { return static_cast<int>(w << 16) >> 16; }
+__device__ __forceinline__ int shift_r(uint32_t w) { return static_cast<int>(w) >> 16; }
+
 // z-buffer entry: ((255 - depth) << 24) | RGB of the source, reduced with atomicMin
 // into a buffer initialised to kEmpty.  The smallest entry has the largest depth
 // (nearest source).  Two sources with equal depth have equal shifts and so never meet
@@ -361,7 +366,7 @@ struct Job {
 // Shared-memory regions of one CTA (laid out for the widest image of the launch).
 struct Shm {
   uint64_t *full;  // ring-slot mbarriers
-  int4 *lut4;      // {-hL, -hR, (255 - d) << 24, 0} per depth
+  uint32_t *lut;   // per depth: -hL in the low 16 bits, -hR in the high 16 bits (two's complement)
   int32_t *lut_n;  // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
   uint8_t *ring, *drow;
   uint32_t *zb0;   // [2 rows][L, R][zlen]
@@ -372,7 +377,7 @@ __device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch_ma
   const BandSmem L = band_smem_layout(nb, srow, nch_max, depth_src);
   Shm m;
   m.full = reinterpret_cast<uint64_t *>(smem + L.bar);
-  m.lut4 = reinterpret_cast<int4 *>(smem + L.lut);
+  m.lut = reinterpret_cast<uint32_t *>(smem + L.lut);
   m.ring = smem + L.ring;
   m.drow = smem + L.drow;
   m.zb0 = reinterpret_cast<uint32_t *>(smem + L.zb);
@@ -387,8 +392,8 @@ __device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch_ma
 __device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, const int32_t *lut_n, bool forward) {
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     const int32_t h = lut_h[i];
-    m.lut4[i] = make_int4(-static_cast<int16_t>(h & 0xFFFF), -(h >> 16),
-                          static_cast<int>((255u - static_cast<uint32_t>(i)) << 24), 0);
+    const int nl = -static_cast<int16_t>(h & 0xFFFF), nr = -(h >> 16);  // |h| <= 512
+    m.lut[i] = (static_cast<uint32_t>(nr) << 16) | (static_cast<uint32_t>(nl) & 0xFFFFu);
     if (!forward) m.lut_n[i] = lut_n[i];
   }
 }
@@ -574,7 +579,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       const uint32_t cws = smem_addr(rgbrow) + (ob & ~3u);  // the lane's colours: +96 bytes per step
       const uint32_t sh = (ob & 3u) * 8u;
       const uint32_t ds = smem_addr(m.drow) + static_cast<uint32_t>(xb);
-      const uint32_t ls = smem_addr(m.lut4);
+      const uint32_t ls = smem_addr(m.lut);
       const uint32_t zls = smem_addr(zl), zrs = smem_addr(zr);
       const bool full_warp = warp_hi - warp_lo == 32 * kChunk;
       if (full_warp) {
@@ -584,14 +589,14 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
           uint32_t dv[4], cw[8];
           lds_u8_step32x4(ds + 128 * g, dv);
           lds_u32_pair_step96x4(cws + 384 * g, cw);
-          int4 lh[4];
+          uint32_t lh[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) lh[j] = lds_s32x4(ls + 16 * dv[j]);
+          for (int j = 0; j < 4; ++j) lh[j] = lds_u32(ls + 4u * dv[j]);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int x = xb + 32 * (4 * g + j);
-            const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh[j].z);
-            const int tl = x + lh[j].x, tr = x + lh[j].y;
+            const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | (~dv[j] << 24);
+            const int tl = x + shift_l(lh[j]), tr = x + shift_r(lh[j]);
             if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
             if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
           }
@@ -603,10 +608,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
           const int x = xb + 32 * i;
           if (x < warp_hi) {
             const uint32_t dv = lds_u8(ds + 32 * i);
-            const int4 lh = lds_s32x4(ls + 16 * dv);
+            const uint32_t lh = lds_u32(ls + 4u * dv);
             const uint32_t w0 = lds_u32(cws + 96 * i), w1 = lds_u32(cws + 96 * i + 4);
-            const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | static_cast<uint32_t>(lh.z);
-            const int tl = x + lh.x, tr = x + lh.y;
+            const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | (~dv << 24);
+            const int tl = x + shift_l(lh), tr = x + shift_r(lh);
             if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
             if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
           }

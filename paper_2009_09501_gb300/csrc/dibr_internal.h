@@ -98,8 +98,8 @@ __host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, 
   BandSmem s;
   s.bar = 0;                       // full[kMaxRing] mbarriers
   s.flags = 8 * kMaxRing;          // batched launches: the current work unit
-  s.lut = s.flags + 64;            // int4 lut[256]: {-hL[d], -hR[d], (255 - d) << 24, 0}
-  s.ring = round_up(s.lut + 4096, 128);
+  s.lut = s.flags + 64;            // uint32 lut[256]: -hL[d] | -hR[d] << 16
+  s.ring = round_up(s.lut + 1024, 128);
   // depth of the current row, one byte per column (read back by the scatter)
   s.drow = round_up(s.ring + nb * srow, 16);
   // z-buffers of the forward warp, double buffered across rows: [2][L, R][nch * 16]
