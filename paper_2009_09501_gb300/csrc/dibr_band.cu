@@ -175,6 +175,13 @@ __device__ __forceinline__ int shift_r(uint32_t w) { return static_cast<int>(w) 
 // among at most 289).
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
+// Packed RGB (3 bytes) of column x of a row in global memory (byte loads: nothing past the
+// pixel is read).
+__device__ __forceinline__ uint32_t rgb_at_global(const uint8_t *row, int x) {
+  const uint8_t *p = row + 3 * static_cast<int64_t>(x);
+  return static_cast<uint32_t>(p[0]) | (static_cast<uint32_t>(p[1]) << 8) | (static_cast<uint32_t>(p[2]) << 16);
+}
+
 // Packed RGB (3 bytes) of column x of a row held in shared memory.
 __device__ __forceinline__ uint32_t rgb_at(const uint8_t *row, int x) {
   const uint32_t off = 3u * static_cast<uint32_t>(x);
@@ -228,7 +235,7 @@ __device__ __noinline__ int warp_walk_right(const uint32_t *zb, int t, int W, in
 // carries in as 0, which is never strictly farther; holes with no left key (row starts)
 // are set afterwards on a path of their own.
 // Returns the thread's hole bits (bit j: no source reached target x0 + j).
-__device__ __forceinline__ uint32_t resolve_view(const uint32_t *zb, const uint8_t *rgbrow, int x0, int npx, int W,
+__device__ __forceinline__ uint32_t resolve_view(const uint32_t *zb, const uint8_t *grow, int x0, int npx, int W,
                                                  int lane, int warp_lo, int warp_hi, uint32_t (&k)[16]) {
   const uint32_t zs = smem_addr(zb);
   if (npx > 0) {
@@ -299,7 +306,7 @@ __device__ __forceinline__ uint32_t resolve_view(const uint32_t *zb, const uint8
     } else {
 #pragma unroll
       for (int j = 0; j < 16; ++j)  // (no bit is set past the row's end)
-        if ((before >> j) & 1u) k[j] = rgb_at(rgbrow, x0 + j);
+        if ((before >> j) & 1u) k[j] = rgb_at_global(grow, x0 + j);
     }
   }
   return holes;
@@ -366,6 +373,7 @@ struct Job {
 // Shared-memory regions of one CTA (laid out for the widest image of the launch).
 struct Shm {
   uint64_t *full;  // ring-slot mbarriers
+  uint64_t *adone; // every warp has stored the next row's depths and cleared its z-buffers
   uint32_t *lut;   // per depth: -hL in the low 16 bits, -hR in the high 16 bits (two's complement)
   int32_t *lut_n;  // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
   uint8_t *ring, *drow;
@@ -377,6 +385,7 @@ __device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch_ma
   const BandSmem L = band_smem_layout(nb, srow, nch_max, depth_src);
   Shm m;
   m.full = reinterpret_cast<uint64_t *>(smem + L.bar);
+  m.adone = reinterpret_cast<uint64_t *>(smem + L.flags + 8);
   m.lut = reinterpret_cast<uint32_t *>(smem + L.lut);
   m.ring = smem + L.ring;
   m.drow = smem + L.drow;
@@ -404,7 +413,7 @@ __device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, co
 // loads issued here.  Returns false when a bounded wait gave up (the status word is
 // set and the copies in flight have been waited for).
 __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
-                                         int *status, unsigned long long timeout_ns) {
+                                         uint32_t &abase, int *status, unsigned long long timeout_ns) {
   const int tid = threadIdx.x, nc = blockDim.x, W = a.W, H = a.H, nb = m.nb;
   const bool binom = a.depth_src == DS_BINOM5;
   const bool forward = a.warp_mode == DIBR_WARP_FORWARD;
@@ -507,11 +516,18 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     else issue_loads((ys - la) + nb);  // the rows above the band are done with
   }
 
-  for (int y = ys; y < ye && !aborted; ++y) {
+  // Per row, three phases: A (depth of the row into shared memory, its z-buffers cleared),
+  // B (the forward warp: every source's entry reduced into the z-buffers), C (winners, hole
+  // fill, formatting, stores).  B of a row needs A of that row done by every warp (a split
+  // barrier: each warp arrives after its A and waits before its B), and C of a row needs B
+  // of that row done by every warp (a full barrier).  A of the next row comes before C of
+  // this one, so a warp that finishes C early scatters the next row while the others still
+  // resolve this one.  C reads this row's input from global memory (the rare cases that
+  // need it), so its ring slot is refilled as soon as B of the row is done.
+  auto phase_a = [&](int y) -> uint4 {
+    uint4 d = make_uint4(0u, 0u, 0u, 0u);
     uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
     uint32_t *zr = zl + m.zlen;
-    // ---- phase A: depth of row y in registers; clear this row's z-buffer targets
-    uint4 d = make_uint4(0u, 0u, 0u, 0u);
     if (binom) {
       const int r2 = y + 2;
       if (r2 < lb) wait_row(r2);
@@ -561,16 +577,12 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         }
       }
     }
-    if (consumer_sync_or(timed_out, nc)) {
-      aborted = true;
-      break;
-    }
-    // every thread is past phase C of row y-1: the slots of rows < y can be refilled
-    issue_loads((y - la) + nb);
-
-    // ---- phase B: forward warp; occlusion by atomicMin on (255 - depth, RGB) entries
+    return d;
+  };
+  auto phase_b = [&](int y) {
     const uint8_t *rgbrow = slot(y);
-    const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
+    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
+    uint32_t *zr = zl + m.zlen;
     if (forward) {
       // the warp's 512 sources, consecutive lanes on consecutive columns, so that the
       // atomics of one instruction land on distinct banks (shifts vary slowly)
@@ -618,14 +630,18 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         }
       }
     }
-    consumer_sync(nc);
-
-    // ---- phase C: resolve winners, fill holes, compose and store the outputs
+  };
+  auto phase_c = [&](int y, uint4 d) {
+    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
+    uint32_t *zr = zl + m.zlen;
+    const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
+    // this row's input from global memory: its ring slot is refilled while this runs
+    const uint8_t *grow = a.in + static_cast<int64_t>(y) * a.in_pitch;
     uint32_t kl[16], kr[16];
     uint32_t hole_l = 0u, hole_r = 0u;
     if (forward) {
-      hole_l = resolve_view(zl, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kl);
-      hole_r = resolve_view(zr, rgbrow, x0, npx, W, lane, warp_lo, warp_hi, kr);
+      hole_l = resolve_view(zl, grow, x0, npx, W, lane, warp_lo, warp_hi, kl);
+      hole_r = resolve_view(zr, grow, x0, npx, W, lane, warp_lo, warp_hi, kr);
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
 #pragma unroll
@@ -635,8 +651,8 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         int sl = (510 * x + n) / 510, sr = (510 * x - n) / 510;
         if (static_cast<unsigned>(sl) >= static_cast<unsigned>(W)) sl = x;
         if (static_cast<unsigned>(sr) >= static_cast<unsigned>(W)) sr = x;
-        kl[i] = active ? rgb_at(rgbrow, sl) : 0u;
-        kr[i] = active ? rgb_at(rgbrow, sr) : 0u;
+        kl[i] = active ? rgb_at_global(grow, sl) : 0u;
+        kr[i] = active ? rgb_at_global(grow, sr) : 0u;
       }
     }
     if (active && want_holes) {
@@ -689,6 +705,45 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         store24(a.out[O_HSBS] + ro + 3 * (W / 2 + x0 / 2), wr, np);
       }
     }
+  };
+  // the split barrier: warps arrive after A of a row; it completes once per row
+  auto a_arrive = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(m.adone);
+  };
+  auto a_wait = [&]() {
+    if (!mbar_wait_bounded(m.adone, abase & 1u, timeout_ns)) timed_out = true;
+    ++abase;
+  };
+
+  uint4 dcur = make_uint4(0u, 0u, 0u, 0u);
+  if (!aborted && ys < ye) {
+    dcur = phase_a(ys);
+    if (consumer_sync_or(timed_out, nc)) aborted = true;
+    else {
+      phase_b(ys);
+      if (consumer_sync_or(timed_out, nc)) aborted = true;
+    }
+  }
+  for (int y = ys; y < ye && !aborted; ++y) {
+    // every thread is past B of row y: the slots of rows <= y can be refilled
+    issue_loads((y - la) + 1 + nb);
+    const bool more = y + 1 < ye;
+    uint4 dnext = make_uint4(0u, 0u, 0u, 0u);
+    if (more) {
+      dnext = phase_a(y + 1);
+      a_arrive();
+    }
+    phase_c(y, dcur);
+    if (more) {
+      a_wait();
+      phase_b(y + 1);
+    }
+    if (consumer_sync_or(timed_out, nc)) {
+      aborted = true;
+      break;
+    }
+    dcur = dnext;
   }
 
   kbase = k0 + issued;
@@ -717,6 +772,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   fill_luts(m, a.lut_h, a.lut_n, a.warp_mode == DIBR_WARP_FORWARD);
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.nb; ++i) mbar_init(&m.full[i], 1);
+    mbar_init(m.adone, blockDim.x / 32);
     fence_mbar_init();
   }
   __syncthreads();
@@ -739,8 +795,8 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   j.W = a.W; j.H = a.H; j.nch = a.nch; j.row_bytes = a.row_bytes; j.load_mode = a.load_mode;
   j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
   j.outputs = a.outputs; j.warp_mode = a.warp_mode; j.depth_src = a.depth_src; j.l2_prefetch = a.l2_prefetch;
-  uint32_t kbase = 0;
-  run_band(j, m, ys, ye, kbase, a.status, a.timeout_ns);
+  uint32_t kbase = 0, abase = 0;
+  run_band(j, m, ys, ye, kbase, abase, a.status, a.timeout_ns);
 }
 
 // ---------------------------------------------------------------------------------
@@ -756,9 +812,10 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
   const Shm m = carve(smem, b.nb, b.srow, b.nch_max, DS_BINOM5);
   if (threadIdx.x == 0) {
     for (int i = 0; i < b.nb; ++i) mbar_init(&m.full[i], 1);
+    mbar_init(m.adone, blockDim.x / 32);
     fence_mbar_init();
   }
-  uint32_t kbase = 0;
+  uint32_t kbase = 0, abase = 0;
   while (true) {
     __syncthreads();  // the previous unit is done with the ring, tables and unit_s
     if (threadIdx.x == 0) *unit_s = atomicAdd(b.counter, 1);
@@ -782,7 +839,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     j.outputs = dsc.outputs; j.warp_mode = dsc.warp_mode; j.depth_src = dsc.depth_src; j.l2_prefetch = 0;
     fill_luts(m, dsc.lut_h, dsc.lut_n, j.warp_mode == DIBR_WARP_FORWARD);
     __syncthreads();
-    if (!run_band(j, m, un.y, un.z, kbase, b.status, b.timeout_ns)) break;
+    if (!run_band(j, m, un.y, un.z, kbase, abase, b.status, b.timeout_ns)) break;
   }
   // A chained launch's CTAs wait for the previous launch to complete before they exit, so
   // that the work after the batch in stream order still follows all of it.
