@@ -254,6 +254,8 @@ dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, 
   smem = band_smem_layout(nb, a.srow, a.nch, depth_src).total;
   per_sm = best;
   a.grid = std::max(1, std::min(H, num_sms * per_sm));
+  a.row0 = 0;
+  a.row1 = H;
   a.status = status_dev;
   a.timeout_ns = timeout_ns;
   return DIBR_OK;
@@ -571,10 +573,119 @@ dibr_status dibr_synthesize_image(dibr_ctx *c, const dibr_image *img, const dibr
 
 }  // extern "C"
 
+// Blocking single-frame path with the input and every output in host memory: the frame is
+// cut into row bands; band k's input copy (copy_in stream), its kernel (the context's
+// stream, once the copies of bands k and k+1 -- two rows of depth context -- have landed)
+// and its output copies (copy_out stream) overlap with the other bands'.  The host link,
+// not the GPU, bounds such a call (about 100 MB cross it per 4K stereo frame), and this
+// keeps both directions of the link busy together.
+dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params *p, const dibr_outputs *o,
+                                        int bands) {
+  const int W = img->width, H = img->height;
+  cudaError_t e;
+  dibr_status s;
+  if (!copy_in) {
+    if (cudaStreamCreateWithFlags(&copy_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&copy_out, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(cudaGetLastError(), "creating the copy streams");
+    for (int k = 0; k < kMaxBands; ++k)
+      if (cudaEventCreateWithFlags(&ev_in[k], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev_comp[k], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "creating the band events");
+  }
+  const int64_t ap = round_up(3 * W, 16), op = round_up(3 * W, 16), dp = round_up(W, 16);
+  if ((s = ensure(stage_in, static_cast<size_t>(ap) * H)) != DIBR_OK) return s;
+  size_t total = 0, offs[O_COUNT];
+  for (int i = 0; i < O_COUNT; ++i) {
+    offs[i] = total;
+    if (p->outputs & kOutBits[i]) total += static_cast<size_t>(is_map_output(i) ? dp : op) * H;
+  }
+  if ((s = ensure(stage_out, total)) != DIBR_OK) return s;
+  BandArgs &a = args;
+  int smem = 0, per_sm = 1;
+  const int depth_src = p->depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
+  if ((s = plan_band(W, H, depth_src, stage_in.ptr, ap, a, smem, per_sm)) != DIBR_OK) return s;
+  if ((s = encode_input(a, stage_in.ptr, ap)) != DIBR_OK) return s;
+  a.depth_in = nullptr;
+  a.depth_in_pitch = 0;
+  for (int i = 0; i < O_COUNT; ++i) a.out[i] = (p->outputs & kOutBits[i]) ? stage_out.ptr + offs[i] : nullptr;
+  a.out_pitch = op;
+  a.depth_pitch = dp;
+  a.outputs = p->outputs;
+  a.warp_mode = p->warp_mode;
+  shift_tables(p, a.lut_h, a.lut_n);
+  const int slots = a.grid;  // CTAs of a whole-frame launch
+  auto band_row = [&](int k) { return static_cast<int>(static_cast<int64_t>(k) * H / bands); };
+  // the copy streams start after the work already queued on the context's stream
+  if ((e = cudaEventRecord(ev_out, stream)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
+  cudaStreamWaitEvent(copy_in, ev_out, 0);
+  cudaStreamWaitEvent(copy_out, ev_out, 0);
+  for (int k = 0; k < bands; ++k) {
+    const int y0 = band_row(k), y1 = band_row(k + 1);
+    e = cudaMemcpy2DAsync(stage_in.ptr + static_cast<int64_t>(y0) * ap, ap, img->rgb + static_cast<int64_t>(y0) * img->pitch,
+                          img->pitch, 3 * static_cast<size_t>(W), y1 - y0, cudaMemcpyHostToDevice, copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], copy_in);
+    if (e != cudaSuccess) return cuda_fail(e, "input upload");
+  }
+  for (int k = 0; k < bands; ++k) {
+    const int y0 = band_row(k), y1 = band_row(k + 1);
+    // rows y0 - 2 .. y1 + 1 of the input: bands up to k + 1
+    cudaStreamWaitEvent(stream, ev_in[k + 1 < bands ? k + 1 : k], 0);
+    a.row0 = y0;
+    a.row1 = y1;
+    a.grid = std::max(1, std::min(y1 - y0, slots));
+    e = launch_band(a, smem, per_sm, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_comp[k], stream);
+    if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
+    ++launches;
+    cudaStreamWaitEvent(copy_out, ev_comp[k], 0);
+    for (int i = 0; i < O_COUNT; ++i) {
+      if (!(p->outputs & kOutBits[i])) continue;
+      const bool map = is_map_output(i);
+      const int64_t hp = map ? o->depth_pitch : o->pitch, sp = map ? dp : op;
+      e = cudaMemcpy2DAsync(out_slot(*o, i) + static_cast<int64_t>(y0) * hp, hp, a.out[i] + static_cast<int64_t>(y0) * sp,
+                            sp, map ? static_cast<size_t>(W) : 3 * static_cast<size_t>(W), y1 - y0,
+                            cudaMemcpyDeviceToHost, copy_out);
+      if (e != cudaSuccess) return cuda_fail(e, "output download");
+    }
+  }
+  a.row0 = 0;
+  a.row1 = H;
+  a.grid = slots;
+  // the call's end: everything on the context's stream after the last download
+  if ((e = cudaEventRecord(ev_out, copy_out)) != cudaSuccess) return cuda_fail(e, "ordering the copies");
+  cudaStreamWaitEvent(stream, ev_out, 0);
+  return read_status();
+}
+
+void dibr_ctx::release_band_pipeline() {
+  if (!copy_in) return;
+  cudaStreamSynchronize(copy_in);
+  cudaStreamSynchronize(copy_out);
+  for (int k = 0; k < kMaxBands; ++k) {
+    if (ev_in[k]) cudaEventDestroy(ev_in[k]);
+    if (ev_comp[k]) cudaEventDestroy(ev_comp[k]);
+    ev_in[k] = ev_comp[k] = nullptr;
+  }
+  if (ev_out) cudaEventDestroy(ev_out);
+  ev_out = nullptr;
+  cudaStreamDestroy(copy_in);
+  cudaStreamDestroy(copy_out);
+  copy_in = copy_out = nullptr;
+}
+
 // Blocking single-frame path: host buffers are staged through context-owned device
 // memory (input H2D, outputs D2H) on the context's stream.
 dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o) {
   const int W = img->width, H = img->height;
+  // row bands when both sides of the call are in host memory and every row band is
+  // independent of the others' results (not with the 2-D fill or the cross-bilateral depth,
+  // which need the whole frame first)
+  const int bands = H >= 2048 ? 4 : H >= 512 ? 2 : 1;
+  if (bands > 1 && !img->on_device && !o->on_device && p->hole_fill == DIBR_FILL_ROW &&
+      p->depth_rule != DIBR_DEPTH_LUMA_XBF)
+    return synthesize_banded(img, p, o, bands);
   dibr_image din = *img;
   dibr_outputs dout = *o;
   cudaError_t e;
@@ -618,6 +729,7 @@ dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params
 }
 
 void dibr_ctx::release_buffers() {
+  release_band_pipeline();
   for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth, &inpaint_scratch}) {
     dev_free(b->ptr);
     b->ptr = nullptr;

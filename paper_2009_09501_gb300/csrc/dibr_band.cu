@@ -779,8 +779,9 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   // the work before this launch on the stream (whose results may be this launch's inputs,
   // or whose inputs this launch's outputs may overwrite) has completed
   griddep_wait();
-  const int ys = static_cast<int>(static_cast<int64_t>(blockIdx.x) * a.H / a.grid);
-  const int ye = static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * a.H / a.grid);
+  const int nr = a.row1 - a.row0;
+  const int ys = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x) * nr / a.grid);
+  const int ye = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nr / a.grid);
   if (ys >= ye) return;
   Job j;
   j.in = a.in;

@@ -53,6 +53,11 @@ struct dibr_ctx {
   size_t batch_pinned_bytes = 0;
   cudaEvent_t batch_copy_done = nullptr;   // the last descriptor upload has read the staging
 
+  // blocking calls with host buffers: copies and kernels of row bands overlap
+  static constexpr int kMaxBands = 8;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in[kMaxBands] = {}, ev_comp[kMaxBands] = {}, ev_out = nullptr;
+
   // serving loop (dibr_serve.cu)
   dibr::ServeState *serve = nullptr;
 
@@ -66,6 +71,8 @@ struct dibr_ctx {
   dibr_status encode_input(dibr::BandArgs &a, const uint8_t *dev_rgb, int64_t pitch);
   dibr_status enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
   dibr_status synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
+  dibr_status synthesize_banded(const dibr_image *img, const dibr_params *p, const dibr_outputs *o, int bands);
+  void release_band_pipeline();
   dibr_status enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
                                    const dibr_outputs *outs);
   dibr_status read_status();

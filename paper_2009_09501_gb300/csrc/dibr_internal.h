@@ -76,7 +76,8 @@ struct BandArgs {
   int32_t nb;        // ring slots
   int32_t nch;       // 16-pixel chunks per row
   int32_t nc;        // threads per CTA, one 16-pixel chunk each (multiple of 32)
-  int32_t grid;      // CTAs; CTA b owns rows [b*H/grid, (b+1)*H/grid)
+  int32_t grid;      // CTAs; CTA b owns rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0
+  int32_t row0, row1;  // the rows this launch computes (all of them: 0, H)
   uint32_t outputs;  // DIBR_OUT_* bits
   int32_t warp_mode; // DIBR_WARP_*
   int32_t depth_src; // DepthSource

@@ -242,3 +242,14 @@ def test_page_locked_host_outputs(ctx, torch, oracle):
         ctx.synthesize_image(np.ascontiguousarray(img), p, {n: v.numpy() for n, v in outs.items()})
         ref = oracle.dibr(img, oracle.params(max_parallax=24, fill_mode=fill, inpaint_block=16), want=want)
         assert_same({n: v.numpy() for n, v in outs.items()}, ref, "pinned host fill=%d" % fill)
+
+
+@pytest.mark.parametrize("W,H,P", [(1920, 1080, 48), (3840, 2160, 64), (1001, 2049, 24), (640, 512, 200)])
+def test_host_buffers_row_bands(ctx, torch, oracle, W, H, P):
+    # blocking calls with host input and outputs run as overlapping row bands
+    img = scenes.Scene(W, H, seed=W + H, n_objects=20).frame(0)
+    want = ("anaglyph", "left", "right", "depth", "holes") + (("hsbs",) if W % 2 == 0 else ())
+    outs = {n: np.zeros((H, W) if n in D.MAP_OUTPUTS else (H, W, 3), np.uint8) for n in want}
+    ctx.synthesize_image(np.ascontiguousarray(img), D.make_params(max_parallax=P, outputs=want), outs)
+    ref = oracle.dibr(img, oracle.params(max_parallax=P), want=want)
+    assert_same(outs, ref, "banded %dx%d" % (W, H))
