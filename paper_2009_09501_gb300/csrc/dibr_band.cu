@@ -857,7 +857,6 @@ cudaError_t allow_smem(K kernel, bool &done) {
 
 }  // namespace
 
-int band_max_threads(int ctas_per_sm) { return ctas_per_sm >= 2 ? 256 : kMaxConsumers; }
 
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
   (void)ctas_per_sm;

@@ -34,10 +34,6 @@ constexpr int kBlocksPerCta = 1;        // image blocks per CTA; one warp per bl
 // range); index n.
 __constant__ uint32_t kHalfRecip[9] = {0, 0, 16384, 10923, 8192, 6554, 5462, 4682, 4096};
 
-__device__ __forceinline__ uint32_t load_rgb(const uint8_t *p) {
-  return static_cast<uint32_t>(p[0]) | (static_cast<uint32_t>(p[1]) << 8) | (static_cast<uint32_t>(p[2]) << 16);
-}
-
 __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
   p[0] = static_cast<uint8_t>(c);
   p[1] = static_cast<uint8_t>(c >> 8);

@@ -12,7 +12,6 @@ namespace dibr {
 
 constexpr int kChunk = 16;          // pixels owned by one consumer thread per pass
 constexpr int kMaxRing = 8;         // TMA row-ring slots at most
-constexpr int kYRing = 6;           // luminance rows kept for the 5-row binomial
 constexpr int kBoxBytes = 256;      // 2-D TMA box width (bytes) for rows with 3*W not a multiple of 16
 constexpr int kMaxConsumers = 512;  // threads per CTA at most (8K rows use 480)
 constexpr int kMaxWidth = 7680;   // 8K UHD: the widest row whose z-buffers and ring fit on chip
@@ -270,7 +269,6 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
 // chained: may start while the previous launch on the stream finishes (the previous
 // launch is a batch launch of the same call).
 cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st);
-int band_max_threads(int ctas_per_sm);
 cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st);
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,
