@@ -240,6 +240,7 @@ def bench_batch(D, torch, ctx, stream, n=64):
     outs = [{"anaglyph": torch.empty_like(t)} for t in ins]
     prms = [D.make_params(max_parallax=scenes.batch_parallax(t.shape[1]), outputs=("anaglyph",)) for t in ins]
     pixels = sum(t.shape[0] * t.shape[1] for t in ins)
+    torch.cuda.synchronize()
 
     def timed(fn, reps=5):
         fn()
@@ -269,6 +270,7 @@ def bench_inpaint(D, torch, ctx, stream, reps=200):
     for _ in range(4):
         i = img.clone()
         sets.append((i, {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS}))
+    torch.cuda.synchronize()
     res = {}
     for name, fill in (("row_fill", D.DIBR_FILL_ROW), ("inpaint2d", D.DIBR_FILL_INPAINT2D)):
         p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, hole_fill=fill, inpaint_block=32)
@@ -297,6 +299,7 @@ def bench_xbf(D, torch, ctx, stream, reps=200):
     H, W = img.shape[:2]
     sets = [(img.clone(), {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS})
             for _ in range(4)]
+    torch.cuda.synchronize()
     res = {}
     for name, rule in (("binom5", D.DIBR_DEPTH_LUMA_BINOM5), ("xbf", D.DIBR_DEPTH_LUMA_XBF)):
         p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, depth_rule=rule)
@@ -425,10 +428,10 @@ def run_ours(args):
 
     img = scenes.config_scene(2)
     H, W = img.shape[:2]
-    # a dedicated stream: the library runs on it and the CUDA events are recorded on it
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    ctx = D.Context(device=local, stream=stream.cuda_stream)
+    # the context's own stream (the library's default): events are recorded on it, and no
+    # other work is enqueued there, so consecutive frames with disjoint buffers may overlap
+    ctx = D.Context(device=local)
+    stream = torch.cuda.ExternalStream(D.dibr_stream(ctx.handle), device=torch.device("cuda", local))
     p = D.make_params(max_parallax=P4K, outputs=OUTPUTS)
 
     # rotate buffer sets so that every step reads and writes HBM, not L2
@@ -442,6 +445,7 @@ def run_ours(args):
         i = src.clone()
         o = {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS}
         sets.append((D.image_struct(i), D.outputs_struct(o), i, o))
+    torch.cuda.synchronize()  # the buffers (made on torch's stream) exist before the library's stream uses them
     lib = D.load()
     enqueue = lib.dibr_enqueue_image
     h = ctx.handle

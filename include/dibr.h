@@ -179,7 +179,11 @@ void dibr_destroy(dibr_ctx *ctx);
 /* Text of the last error recorded on ctx ("" if none).  Valid until the next call. */
 const char *dibr_last_error(dibr_ctx *ctx);
 
-/* The context's CUDA stream (a cudaStream_t). */
+/* The context's CUDA stream (a cudaStream_t).  When the context created it
+ * (dibr_config.cuda_stream NULL), the caller may record events on it and wait for it but
+ * enqueues no work of its own there; consecutive dibr_enqueue_image calls whose buffers
+ * are disjoint then overlap: the next frame starts in the SMs the previous one has left
+ * (a frame still completes only after the one before it). */
 void *dibr_stream(dibr_ctx *ctx);
 
 /* One frame, blocking: returns when the outputs are written (host or device).  Host

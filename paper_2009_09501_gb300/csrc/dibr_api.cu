@@ -52,6 +52,7 @@ void dibr_ctx::dev_free(void *p) {
 
 dibr_status dibr_ctx::ensure(DevBuf &b, size_t bytes) {
   if (b.bytes >= bytes && b.ptr) return DIBR_OK;
+  prev_band = false;  // the stream-ordered free and allocation below are work on the stream
   if (b.ptr) {
     cudaStreamSynchronize(stream);
     dev_free(b.ptr);
@@ -256,6 +257,7 @@ dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, 
   a.grid = std::max(1, std::min(H, num_sms * per_sm));
   a.row0 = 0;
   a.row1 = H;
+  a.overlap = 0;
   a.status = status_dev;
   a.timeout_ns = timeout_ns;
   return DIBR_OK;
@@ -303,7 +305,13 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   const int W = img->width, H = img->height;
   const uint8_t *in = img->rgb;
   int64_t pitch = img->pitch;
+  // this launch may overlap the previous one (see below) only if that was the last work
+  // on a stream the context owns
+  const bool may_overlap = owns_stream && prev_band;
+  prev_band = false;
+  bool scratch = false;  // context buffers written before the band kernel
   if (!tma_ok(in, pitch)) {
+    scratch = true;
     // TMA needs a 16-byte aligned base and pitch: repack into an aligned device buffer
     const int64_t ap = round_up(3 * W, 16);
     dibr_status s = ensure(realign, static_cast<size_t>(ap) * H);
@@ -323,6 +331,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   if (s != DIBR_OK) return s;
   if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
   if (depth_src == DS_GLOBAL) {
+    scratch = true;
     const int64_t dp = round_up(W, 16);
     if ((s = ensure(xbf_depth, static_cast<size_t>(dp) * H)) != DIBR_OK) return s;
     cudaError_t e = launch_xbf(in, pitch, W, H, p->xbf_radius, p->xbf_sigma_s, p->xbf_sigma_r,
@@ -367,9 +376,40 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     a.outputs |= DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HOLES;
   }
   shift_tables(p, a.lut_h, a.lut_n);
+  // Overlap with the previous band launch on the stream when neither reads or writes what
+  // the other writes: this launch then starts in the SMs the previous one leaves and only
+  // its exit waits for it.
+  auto span = [](const uint8_t *ptr, int64_t row_pitch, int rows, int64_t row_bytes) {
+    Span sp;
+    sp.lo = reinterpret_cast<uintptr_t>(ptr);
+    sp.hi = sp.lo + static_cast<uintptr_t>(row_pitch) * (rows - 1) + static_cast<uintptr_t>(row_bytes);
+    return sp;
+  };
+  auto meets = [](const Span &x, const Span &y) { return x.lo < y.hi && y.lo < x.hi; };
+  Span cur_in = span(in, pitch, H, 3 * static_cast<int64_t>(W)), cur_out[O_COUNT];
+  for (int i = 0; i < O_COUNT; ++i)
+    cur_out[i] = (a.outputs & kOutBits[i]) && a.out[i]
+                     ? span(a.out[i], is_map_output(i) ? a.depth_pitch : a.out_pitch, H,
+                            is_map_output(i) ? static_cast<int64_t>(W) : 3 * static_cast<int64_t>(W))
+                     : Span{};
+  bool disjoint = may_overlap && !scratch && !inpaint;
+  for (int i = 0; i < O_COUNT; ++i) {
+    if (prev_out[i].hi && meets(cur_in, prev_out[i])) disjoint = false;  // reads what it wrote
+    if (!cur_out[i].hi) continue;
+    if (meets(cur_out[i], prev_in)) disjoint = false;  // writes what it read
+    for (int j = 0; j < O_COUNT; ++j)
+      if (prev_out[j].hi && meets(cur_out[i], prev_out[j])) disjoint = false;  // writes what it wrote
+  }
+  a.overlap = disjoint ? 1 : 0;
   cudaError_t e = launch_band(a, smem, per_sm, stream);
+  a.overlap = 0;
   if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
   ++launches;
+  if (!inpaint) {
+    prev_band = true;
+    prev_in = cur_in;
+    for (int i = 0; i < O_COUNT; ++i) prev_out[i] = cur_out[i];
+  }
   if (inpaint) {
     InpaintArgs ia;
     ia.view[0] = a.out[O_LEFT];
@@ -393,6 +433,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
 }
 
 dibr_status dibr_ctx::read_status() {
+  prev_band = false;
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, status_dev, sizeof(int), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -582,6 +623,7 @@ dibr_status dibr_synthesize_image(dibr_ctx *c, const dibr_image *img, const dibr
 dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params *p, const dibr_outputs *o,
                                         int bands) {
   const int W = img->width, H = img->height;
+  prev_band = false;
   cudaError_t e;
   dibr_status s;
   if (!copy_in) {
@@ -679,6 +721,7 @@ void dibr_ctx::release_band_pipeline() {
 // memory (input H2D, outputs D2H) on the context's stream.
 dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o) {
   const int W = img->width, H = img->height;
+  prev_band = false;  // copies precede the launch
   // row bands when both sides of the call are in host memory and every row band is
   // independent of the others' results (not with the 2-D fill or the cross-bilateral depth,
   // which need the whole frame first)

@@ -777,12 +777,17 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   }
   __syncthreads();
   // the work before this launch on the stream (whose results may be this launch's inputs,
-  // or whose inputs this launch's outputs may overwrite) has completed
-  griddep_wait();
+  // or whose inputs this launch's outputs may overwrite) has completed -- unless the host
+  // knows this launch touches none of that launch's buffers; then the wait moves to the
+  // end, so that this launch still completes after the previous one
+  if (!a.overlap) griddep_wait();
   const int nr = a.row1 - a.row0;
   const int ys = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x) * nr / a.grid);
   const int ye = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nr / a.grid);
-  if (ys >= ye) return;
+  if (ys >= ye) {
+    if (a.overlap) griddep_wait();
+    return;
+  }
   Job j;
   j.in = a.in;
   j.in_pitch = a.in_pitch;
@@ -798,6 +803,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   j.outputs = a.outputs; j.warp_mode = a.warp_mode; j.depth_src = a.depth_src; j.l2_prefetch = a.l2_prefetch;
   uint32_t kbase = 0, abase = 0;
   run_band(j, m, ys, ye, kbase, abase, a.status, a.timeout_ns);
+  if (a.overlap) griddep_wait();
 }
 
 // ---------------------------------------------------------------------------------

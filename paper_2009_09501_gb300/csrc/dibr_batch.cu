@@ -45,6 +45,7 @@ void dibr_ctx::release_batch_buffers() {
 // All buffers in device memory.  Enqueues the batch on the context's stream.
 dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
                                            const dibr_outputs *outs) {
+  prev_band = false;
   if (n == 0) return DIBR_OK;
   // --- inputs that a bulk row copy cannot read directly are repacked (16-byte rows)
   std::vector<const uint8_t *> in(n);

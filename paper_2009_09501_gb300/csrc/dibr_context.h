@@ -53,6 +53,14 @@ struct dibr_ctx {
   size_t batch_pinned_bytes = 0;
   cudaEvent_t batch_copy_done = nullptr;   // the last descriptor upload has read the staging
 
+  // the buffers of the last single-frame band launch, when it is the last work on a stream
+  // the context owns (the next launch may overlap it if their buffers are disjoint)
+  struct Span {
+    uintptr_t lo = 0, hi = 0;
+  };
+  bool prev_band = false;
+  Span prev_in, prev_out[dibr::O_COUNT];
+
   // blocking calls with host buffers: copies and kernels of row bands overlap
   static constexpr int kMaxBands = 8;
   cudaStream_t copy_in = nullptr, copy_out = nullptr;

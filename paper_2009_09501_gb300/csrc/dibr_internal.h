@@ -77,6 +77,8 @@ struct BandArgs {
   int32_t nc;        // threads per CTA, one 16-pixel chunk each (multiple of 32)
   int32_t grid;      // CTAs; CTA b owns rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0
   int32_t row0, row1;  // the rows this launch computes (all of them: 0, H)
+  int32_t overlap;   // 1: independent of the previous launch on the stream (start at once;
+                     // wait for it only before exiting); 0: wait for it before any global access
   uint32_t outputs;  // DIBR_OUT_* bits
   int32_t warp_mode; // DIBR_WARP_*
   int32_t depth_src; // DepthSource

@@ -302,10 +302,25 @@ class Context:
     def stream(self):
         return dibr_stream(self._ctx)
 
+    @staticmethod
+    def _after_torch(*objs):
+        # torch's work on CUDA tensors (made or written on torch's stream) completes before
+        # the context's own stream touches them
+        for o in objs:
+            for t in (o.values() if isinstance(o, dict) else o if isinstance(o, (list, tuple)) else (o,)):
+                if isinstance(t, dict):
+                    Context._after_torch(t)
+                elif _is_torch(t) and t.is_cuda:
+                    import torch
+                    torch.cuda.current_stream(t.device).synchronize()
+                    return
+
     def synthesize_image(self, img, p, outs, in_pitch=None):
+        self._after_torch(img, outs)
         return self.check(dibr_synthesize_image(self._ctx, image_struct(img, in_pitch), p, outputs_struct(outs)))
 
     def enqueue_image(self, img, p, outs, in_pitch=None):
+        self._after_torch(img, outs)
         return self.check(dibr_enqueue_image(self._ctx, image_struct(img, in_pitch), p, outputs_struct(outs)))
 
     def synchronize(self):
@@ -321,10 +336,12 @@ class Context:
         return n, I, Pa, len(params), O
 
     def synthesize_batch(self, imgs, params, outs):
+        self._after_torch(imgs, outs)
         n, I, Pa, npar, O = self._batch_args(imgs, params, outs)
         return self.check(dibr_synthesize_batch(self._ctx, n, I, Pa, npar, O))
 
     def enqueue_batch(self, imgs, params, outs):
+        self._after_torch(imgs, outs)
         n, I, Pa, npar, O = self._batch_args(imgs, params, outs)
         return self.check(dibr_enqueue_batch(self._ctx, n, I, Pa, npar, O))
 

@@ -253,3 +253,29 @@ def test_host_buffers_row_bands(ctx, torch, oracle, W, H, P):
     ctx.synthesize_image(np.ascontiguousarray(img), D.make_params(max_parallax=P, outputs=want), outs)
     ref = oracle.dibr(img, oracle.params(max_parallax=P), want=want)
     assert_same(outs, ref, "banded %dx%d" % (W, H))
+
+
+def test_back_to_back_frames_overlap_only_when_independent(ctx, torch, oracle):
+    # consecutive asynchronous frames on the context's own stream: disjoint buffers may
+    # overlap on the GPU, a frame reading the previous frame's output must not
+    H, W, P = 720, 1280, 32
+    imgs = [scenes.Scene(W, H, seed=500 + k, n_objects=15).frame(0) for k in range(4)]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [{"anaglyph": torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda"),
+             "left": torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda")} for _ in imgs]
+    chained = {"anaglyph": torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda")}
+    p = gpu_params(("anaglyph", "left"), max_parallax=P)
+    pc = gpu_params(("anaglyph",), max_parallax=P)
+    torch.cuda.synchronize()
+    lib = D.load()
+    for rep in range(3):
+        for k in range(4):
+            assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(ins[k]), p, D.outputs_struct(outs[k])) == 0
+        # reads the left view frame 3 just wrote
+        assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(outs[3]["left"]), pc, D.outputs_struct(chained)) == 0
+    ctx.synchronize()
+    for k in range(4):
+        ref = oracle.dibr(imgs[k], oracle_params(oracle, max_parallax=P), want=("anaglyph", "left"))
+        assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, ref, "frame %d" % k)
+    ref2 = oracle.dibr(outs[3]["left"].cpu().numpy(), oracle_params(oracle, max_parallax=P), want=("anaglyph",))
+    assert_same({"anaglyph": chained["anaglyph"].cpu().numpy()}, ref2, "chained frame")
