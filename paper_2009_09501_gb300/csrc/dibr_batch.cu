@@ -1,11 +1,12 @@
-// dibr_batch.cu -- images of uneven sizes in one persistent launch (dibr_synthesize_batch,
-// dibr_enqueue_batch).
+// dibr_batch.cu -- images of uneven sizes in one call (dibr_synthesize_batch,
+// dibr_enqueue_batch; also the serving loop's batches).
 //
-// Each image is cut into work units of a few rows (plan_unit_rows).  The host writes one
-// descriptor per image (pointers, sizes, shift tables) and the unit list, largest images
-// first, into device memory with a single copy; the persistent CTAs of the batch kernel
-// take units from a device counter until none is left, so the launch balances itself
-// over images of any mix of sizes.
+// Images that fill the GPU on their own get a band launch each, back to back.  The others
+// are cut into work units of a few rows (plan_unit_rows); the host writes one descriptor
+// per image (pointers, sizes, shift tables) and the unit list, largest images first, into
+// device memory with a single copy; the persistent CTAs of the batch kernel (one chained
+// launch per block-width group) take units from a device counter until none is left, so
+// the launches balance themselves over images of any mix of sizes.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -42,9 +43,56 @@ void dibr_ctx::release_batch_buffers() {
   }
 }
 
-// All buffers in device memory.  Enqueues the batch on the context's stream.
+// All buffers in device memory.  Images large enough to fill the GPU on their own (at
+// least kOwnLaunchRows rows per CTA slot of their launch plan; e.g. 4K and 8K frames) get a
+// band launch each, back to back, overlapping one another when their buffers are disjoint;
+// measured, that beats the persistent launch for them.  The others (e.g. 1080p, 720p) share
+// the grouped persistent launches, which beat per-image launches for them.
+constexpr int kOwnLaunchRows = 4;
+
 dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
                                            const dibr_outputs *outs) {
+  if (n == 0) return DIBR_OK;
+  std::vector<int> own, shared;
+  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm};
+  for (int i = 0; i < n; ++i) {
+    const int w = imgs[i].width, rb = round_up(3 * w, 16);
+    int cl = 0;
+    BatchClass c[1];
+    const bool fits = plan_batch_classes(1, &w, &rb, lim, &cl, c) == 1;
+    const int64_t slots = static_cast<int64_t>(num_sms) * (fits ? c[0].per : 1);
+    const bool big = fits && tuning.rows_per_unit == 0 && imgs[i].height >= kOwnLaunchRows * slots;
+    (big ? own : shared).push_back(i);
+  }
+  dibr_status s = DIBR_OK;
+  if (!shared.empty()) {
+    if (own.empty()) {
+      s = enqueue_grouped(n, imgs, p, n_params, outs);
+    } else {
+      std::vector<dibr_image> si;
+      std::vector<dibr_params> sp;
+      std::vector<dibr_outputs> so;
+      for (int i : shared) {
+        si.push_back(imgs[i]);
+        so.push_back(outs[i]);
+        if (n_params != 1) sp.push_back(p[i]);
+      }
+      s = enqueue_grouped(static_cast<int>(si.size()), si.data(), n_params == 1 ? p : sp.data(),
+                          n_params == 1 ? 1 : static_cast<int>(sp.size()), so.data());
+    }
+    if (s != DIBR_OK) return s;
+  }
+  std::stable_sort(own.begin(), own.end(), [&](int a, int b) {
+    return static_cast<int64_t>(imgs[a].width) * imgs[a].height > static_cast<int64_t>(imgs[b].width) * imgs[b].height;
+  });
+  for (int i : own)
+    if ((s = enqueue_device(&imgs[i], &p[n_params == 1 ? 0 : i], &outs[i])) != DIBR_OK) return s;
+  return DIBR_OK;
+}
+
+// The grouped persistent launches (all buffers in device memory).
+dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                                      const dibr_outputs *outs) {
   prev_band = false;
   if (n == 0) return DIBR_OK;
   // --- inputs that a bulk row copy cannot read directly are repacked (16-byte rows)

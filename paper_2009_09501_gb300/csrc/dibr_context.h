@@ -83,6 +83,8 @@ struct dibr_ctx {
   void release_band_pipeline();
   dibr_status enqueue_batch_device(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
                                    const dibr_outputs *outs);
+  dibr_status enqueue_grouped(int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                              const dibr_outputs *outs);
   dibr_status read_status();
   void release_buffers();
   void release_batch_buffers();
