@@ -63,39 +63,47 @@ __device__ __forceinline__ uint32_t luma_px(uint32_t c) { return luma_dp<0>(c); 
 // shared memory, as 10 words of two 16-bit lanes: yp[2q] = columns (4q, 4q+2) and
 // yp[2q+1] = (4q+1, 4q+3) of the window, the layout the vertical cascade works on.
 __device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32_t (&yp)[10]) {
+  // bytes 3*x0-8 .. 3*x0+55 (8-byte and 16-byte aligned loads); column j of the window at
+  // byte 2+3j.  At the row's ends the loads reach past it into neighbouring shared memory
+  // (the ring's other slots, the table before it, the depth row after it); those columns
+  // are replaced below by the row's first or last column.
   uint32_t y[20];
-  if (x0 >= 16 && x0 + 18 <= W) {
-    // bytes 3*x0-8 .. 3*x0+55 (8-byte and 16-byte aligned loads); column j at byte 2+3j
-    uint32_t b[16];
-    const uint2 l = *reinterpret_cast<const uint2 *>(row + 3 * x0 - 8);
-    const uint4 m0 = *reinterpret_cast<const uint4 *>(row + 3 * x0);
-    const uint4 m1 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 16);
-    const uint4 m2 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 32);
-    const uint2 r = *reinterpret_cast<const uint2 *>(row + 3 * x0 + 48);
-    b[0] = l.x; b[1] = l.y;
-    b[2] = m0.x; b[3] = m0.y; b[4] = m0.z; b[5] = m0.w;
-    b[6] = m1.x; b[7] = m1.y; b[8] = m1.z; b[9] = m1.w;
-    b[10] = m2.x; b[11] = m2.y; b[12] = m2.z; b[13] = m2.w;
-    b[14] = r.x; b[15] = r.y;
+  uint32_t b[16];
+  const uint2 l = *reinterpret_cast<const uint2 *>(row + 3 * x0 - 8);
+  const uint4 m0 = *reinterpret_cast<const uint4 *>(row + 3 * x0);
+  const uint4 m1 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 16);
+  const uint4 m2 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 32);
+  const uint2 r = *reinterpret_cast<const uint2 *>(row + 3 * x0 + 48);
+  b[0] = l.x; b[1] = l.y;
+  b[2] = m0.x; b[3] = m0.y; b[4] = m0.z; b[5] = m0.w;
+  b[6] = m1.x; b[7] = m1.y; b[8] = m1.z; b[9] = m1.w;
+  b[10] = m2.x; b[11] = m2.y; b[12] = m2.z; b[13] = m2.w;
+  b[14] = r.x; b[15] = r.y;
 #pragma unroll
-    for (int j = 0; j < 20; ++j) {
-      const int o = 2 + 3 * j, q = o >> 2;
-      if ((o & 3) == 0) y[j] = luma_dp<0>(b[q]);
-      else if ((o & 3) == 1) y[j] = luma_dp<8>(b[q]);
-      else y[j] = luma_dp<0>(__funnelshift_r(b[q], b[q + 1], 8 * (o & 3)));
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 20; ++j) {
-      const int xc = min(max(x0 - 2 + j, 0), W - 1);
-      const uint8_t *p = row + 3 * xc;
-      y[j] = luma8(p[0], p[1], p[2]);
-    }
+  for (int j = 0; j < 20; ++j) {
+    const int o = 2 + 3 * j, q = o >> 2;
+    if ((o & 3) == 0) y[j] = luma_dp<0>(b[q]);
+    else if ((o & 3) == 1) y[j] = luma_dp<8>(b[q]);
+    else y[j] = luma_dp<0>(__funnelshift_r(b[q], b[q + 1], 8 * (o & 3)));
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     yp[2 * q] = y[4 * q] | (y[4 * q + 2] << 16);
     yp[2 * q + 1] = y[4 * q + 1] | (y[4 * q + 3] << 16);
+  }
+  if (x0 < 2 || x0 + 18 > W) {  // clamp to the row: columns before 0 and after W-1
+    const uint8_t *pl = row + 3 * (W - 1);
+    const uint32_t ylast = luma8(pl[0], pl[1], pl[2]);
+    const uint32_t yfirst = yp[0] >> 16;  // window column 2: column 0 when x0 == 0
+#pragma unroll
+    for (int j = 0; j < 20; ++j) {
+      const int xc = x0 - 2 + j;
+      const int w = 2 * (j >> 2) + (j & 1), sh = 16 * ((j >> 1) & 1);  // word and lane of column j
+      if (xc < 0 || xc > W - 1) {
+        const uint32_t v = xc < 0 ? yfirst : ylast;
+        yp[w] = (yp[w] & ~(0xFFFFu << sh)) | (v << sh);
+      }
+    }
   }
 }
 
