@@ -91,18 +91,24 @@ __device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32
     yp[2 * q] = y[4 * q] | (y[4 * q + 2] << 16);
     yp[2 * q + 1] = y[4 * q + 1] | (y[4 * q + 3] << 16);
   }
-  if (x0 < 2 || x0 + 18 > W) {  // clamp to the row: columns before 0 and after W-1
+  // clamp to the row: the columns before 0 and after W-1 take column 0 and column W-1
+  // (window column j sits in word 2 * (j / 4) + j % 2, high lane when j / 2 is odd)
+  if (x0 == 0) {  // window columns 0 and 1 (low lanes of words 0 and 1) <- window column 2
+    const uint32_t yf = yp[0] >> 16;
+    yp[0] = (yp[0] & 0xFFFF0000u) | yf;
+    yp[1] = (yp[1] & 0xFFFF0000u) | yf;
+  }
+  if (x0 + 16 == W) {  // window columns 18 and 19 (high lanes of words 8, 9) <- column 17
+    const uint32_t yl = yp[9] << 16;
+    yp[8] = (yp[8] & 0xFFFFu) | yl;
+    yp[9] = (yp[9] & 0xFFFFu) | yl;
+  } else if (x0 + 18 > W) {
     const uint8_t *pl = row + 3 * (W - 1);
     const uint32_t ylast = luma8(pl[0], pl[1], pl[2]);
-    const uint32_t yfirst = yp[0] >> 16;  // window column 2: column 0 when x0 == 0
 #pragma unroll
-    for (int j = 0; j < 20; ++j) {
-      const int xc = x0 - 2 + j;
-      const int w = 2 * (j >> 2) + (j & 1), sh = 16 * ((j >> 1) & 1);  // word and lane of column j
-      if (xc < 0 || xc > W - 1) {
-        const uint32_t v = xc < 0 ? yfirst : ylast;
-        yp[w] = (yp[w] & ~(0xFFFFu << sh)) | (v << sh);
-      }
+    for (int j = 3; j < 20; ++j) {
+      const int w = 2 * (j >> 2) + (j & 1), sh = 16 * ((j >> 1) & 1);
+      if (x0 - 2 + j > W - 1) yp[w] = (yp[w] & ~(0xFFFFu << sh)) | (ylast << sh);
     }
   }
 }
@@ -436,28 +442,29 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   auto ring_div = [&](uint32_t g) { return __umulhi(g, ring_rcp); };
 
   // Row k = r - la of the band is the (k0 + k)-th load of this CTA: slot (k0+k) % nb.
-  // Warp 0 issues the loads of rows [issued, upto); the caller guarantees every
-  // earlier occupant of those slots has been released by all threads (a barrier
-  // separates the last use from the call).
+  // The middle warp issues the loads of rows [issued, upto) (the warps at the row's ends
+  // have the most fill work); the caller guarantees every earlier occupant of those slots
+  // has been released by all threads (a barrier separates the last use from the call).
   int issued = 0;
+  const int lw = 32 * ((nc >> 5) >> 1);  // first thread of the loading warp
   auto issue_loads = [&](int upto) {
     upto = min(upto, nload);
-    if (tid < 32) {
-      if (tid == 0 && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
+    if (tid - lw >= 0 && tid - lw < 32) {
+      if (tid == lw && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
       for (int k = issued; k < upto; ++k) {
         const uint32_t g = k0 + k;
         const int s = static_cast<int>(g - ring_div(g) * nb);
         uint8_t *dst = m.ring + s * m.srow;
         if (a.load_mode == LM_BULK) {
-          if (tid == 0) {
+          if (tid == lw) {
             mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.row_bytes));
             bulk_load(dst, a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes),
                       &m.full[s]);
           }
         } else {
-          if (tid == 0) mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
+          if (tid == lw) mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
           __syncwarp();
-          for (int i = tid; i < a.nbox; i += 32) {
+          for (int i = tid - lw; i < a.nbox; i += 32) {
             if (a.load_mode == LM_T3)
               tma_load_3d(dst + i * a.box_bytes, a.tmap, 0, i * a.box_step, la + k, &m.full[s]);
             else
@@ -470,12 +477,12 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   };
   issue_loads(nb);
   // optionally, the band's later rows go to L2 now
-  if (a.l2_prefetch && tid < 32) {
+  if (a.l2_prefetch && tid - lw >= 0 && tid - lw < 32) {
     if (a.load_mode == LM_BULK) {
-      for (int k = nb + tid; k < nload; k += 32)
+      for (int k = nb + tid - lw; k < nload; k += 32)
         bulk_prefetch_l2(a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes));
     } else {
-      for (int j = tid; j < (nload - nb) * a.nbox; j += 32) {
+      for (int j = tid - lw; j < (nload - nb) * a.nbox; j += 32) {
         const int k = nb + j / a.nbox, i = j % a.nbox;
         if (a.load_mode == LM_T3) tma_prefetch_3d(a.tmap, 0, i * a.box_step, la + k);
         else tma_prefetch_2d(a.tmap, i * a.box_step, la + k);
@@ -622,18 +629,32 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
           }
         }
       } else {
-        // the row's last, partial warp: columns from warp_hi on do not exist
-#pragma unroll 4
-        for (int i = 0; i < kChunk; ++i) {
-          const int x = xb + 32 * i;
-          if (x < warp_hi) {
-            const uint32_t dv = lds_u8(ds + 32 * i);
-            const uint32_t lh = lds_u32(ls + 4u * dv);
-            const uint32_t w0 = lds_u32(cws + 96 * i), w1 = lds_u32(cws + 96 * i + 4);
-            const uint32_t e = (__funnelshift_r(w0, w1, sh) & 0xFFFFFFu) | (~dv << 24);
-            const int tl = x + shift_l(lh), tr = x + shift_r(lh);
-            if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
-            if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+        // the row's last, partial warp: columns from warp_hi on do not exist (their loads
+        // read column warp_hi - 1, so that they stay in the row; their atomics are skipped)
+        const uint32_t rs = smem_addr(rgbrow), dr = smem_addr(m.drow);
+#pragma unroll 1
+        for (int g = 0; g < kChunk / 4; ++g) {
+          uint32_t dv[4], cw[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t xc = static_cast<uint32_t>(min(xb + 32 * (4 * g + j), warp_hi - 1));
+            const uint32_t ca = rs + ((3u * xc) & ~3u);
+            dv[j] = lds_u8(dr + xc);
+            cw[2 * j] = lds_u32(ca);
+            cw[2 * j + 1] = lds_u32(ca + 4);
+          }
+          uint32_t lh[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) lh[j] = lds_u32(ls + 4u * dv[j]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int x = xb + 32 * (4 * g + j);
+            if (x < warp_hi) {
+              const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | (~dv[j] << 24);
+              const int tl = x + shift_l(lh[j]), tr = x + shift_r(lh[j]);
+              if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
+              if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+            }
           }
         }
       }
