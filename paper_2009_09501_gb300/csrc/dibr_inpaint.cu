@@ -2,14 +2,14 @@
 // the holes of both reconstructed views after the band kernel (hole fill DIBR_FILL_INPAINT2D).
 //
 // Per block of B x B pixels and per view, one warp.  The figure's algorithm visits the
-// block's damaged pixels block column by block column, repeatedly, and repairs a pixel
-// once two or more of its 8 neighbours are undamaged; a repair is visible at once to the
-// pixels visited after it.  The warp runs that sequential order as a wavefront: lane x
-// owns block column x and at step s handles row s - 2x.  Along the visiting order every
-// neighbour of (x, y) that comes earlier -- column x-1 entirely, and (x, y-1) -- has a
-// smaller step (2x + y - 1 or less), every later one -- column x+1, and (x, y+1) -- a
-// larger step, and no two neighbours share a step; so each step sees exactly the state
-// the sequential visit would see, and the result is the same.
+// block's damaged pixels block column by block column, in passes that repeat while some
+// pixel is repaired, and repairs a pixel once two or more of its 8 neighbours are
+// undamaged; a repair is visible at once to the visits after it.  The warp runs that order
+// as a wavefront with the passes pipelined: lane x owns block column x, and pass p visits
+// row y of it at step 2x + y + 4p.  Every visit sees exactly the state the sequential
+// passes would show it, and the visits of one step are never neighbours (see the loop), so
+// a block whose repairs creep one column per pass (the undamaged side to the right of a
+// wide hole) takes about 2B + B + 4 x passes steps instead of B steps per pass.
 //
 // The damage flags of a column live in a 64-bit register of its lane (bit j = block row
 // j - 1, with the rows above and below the block at bits 0 and B + 1); a lane reads its
@@ -154,19 +154,17 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
       const uint32_t br = static_cast<uint32_t>(rm >> r) & 7u;
       const int n = 8 - __popc(bl) - __popc(bo) - __popc(br);
       if (n < 2) return false;
-      uint32_t srb = 0, sg = 0;  // red and blue sums in two 16-bit lanes, green alone
-#pragma unroll
-      for (int dj = 0; dj < 3; ++dj) {
-#pragma unroll
-        for (int di = 0; di < 3; ++di) {
-          const uint32_t m = di == 0 ? bl : di == 1 ? bo : br;
-          if (di == 1 && dj == 1) continue;
-          if ((m >> dj) & 1u) continue;
-          const uint32_t c = cell[(r + dj) * kStride + lane + di];
-          srb += c & 0x00FF00FFu;
-          sg += __byte_perm(c, 0u, 0x4441u);
-        }
-      }
+      // A damaged cell holds 0 until it is repaired (and then its flag is cleared with the
+      // same visit), so the sums over all eight neighbours are the sums over the undamaged
+      // ones.  Per channel at most 8 * 255 < 2^11: the red and blue sums fit 16-bit lanes
+      // of one word, and the green sum is what the plain word sum has beyond them.
+      const uint32_t *c0 = cell + r * kStride + lane;
+      const uint32_t c[8] = {c0[0], c0[1], c0[2], c0[kStride], c0[kStride + 2], c0[2 * kStride],
+                             c0[2 * kStride + 1], c0[2 * kStride + 2]};
+      const uint32_t all = ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+      const uint32_t srb = (((c[0] & 0x00FF00FFu) + (c[1] & 0x00FF00FFu)) + ((c[2] & 0x00FF00FFu) + (c[3] & 0x00FF00FFu))) +
+                           (((c[4] & 0x00FF00FFu) + (c[5] & 0x00FF00FFu)) + ((c[6] & 0x00FF00FFu) + (c[7] & 0x00FF00FFu)));
+      const uint32_t sg = (all - srb) >> 8;
       // per channel floor((2 sum + n) / 2n): the mean rounded half up
       const uint32_t rc = kHalfRecip[n];
       const uint32_t mr = ((2u * (srb & 0xFFFFu) + n) * rc) >> 16, mb = ((2u * (srb >> 16) + n) * rc) >> 16;
@@ -175,80 +173,54 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
       own &= ~(1ull << (r + 1));
       return true;
     };
-    // the steps at which some lane visits a pixel of mask bits `sel`: lane x visits block
-    // row r at step 2x + r (steps 0..93, three words)
-    auto steps_of = [&](uint64_t sel, uint32_t (&act)[3]) {
-      const uint64_t dm = lane < bw ? (sel & rows) >> 1 : 0ull;
-      const int sh = 2 * lane;
-      const uint64_t lo = dm << sh, hi = sh ? dm >> (64 - sh) : 0ull;
-      act[0] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo));
-      act[1] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(lo >> 32));
-      act[2] = __reduce_or_sync(0xffffffffu, static_cast<uint32_t>(hi));
+    // ---- the passes, pipelined.  Pass p visits block pixel (x, y) at step 2x + y + 4p.
+    // A visit reads only the eight neighbours; in the sequential order those earlier in the
+    // list (column x-1, and (x, y-1)) were last visited by the same pass at a smaller step,
+    // and those later in it (column x+1, and (x, y+1)) by the previous pass at most 3 steps
+    // later in the wavefront than (x, y) itself, i.e. at a step 1 or more below this visit's,
+    // and by this pass at a larger step.  So every visit sees exactly the state the
+    // sequential passes would show it.  Two visits of one step are never neighbours (same
+    // column: rows 4 apart; adjacent columns: rows 2 apart modulo 4), so each step's visits
+    // are independent, and lane x makes those of its column: rows y = T - 2x - 4p, p >= 0.
+    // A damaged pixel whose neighbourhood has not changed since it last failed the test
+    // fails it again, so only "dirty" pixels are visited (never visited yet, or next to a
+    // repair since their last visit); when no damaged pixel is dirty nothing can change any
+    // more, which is where the figure's loop ends too (a pass that repairs nothing).  Steps
+    // at which no lane has a dirty pixel to visit are skipped.
+    uint64_t dirty = own & rows;
+    refresh();
+    const int x2 = 2 * lane;
+    // frame rows j (block row j - 1) that lane x has reached by step t: j - 1 <= t - 2x
+    auto reached = [&](int t) -> uint64_t {
+      const int b = t - x2;
+      return b < 0 ? 0ull : b >= 32 ? ~0ull : (4ull << b) - 1ull;
     };
-
-    // ---- first pass: every damaged pixel is visited
-    uint64_t rep1 = 0;
-    {
-      uint32_t act[3];
-      steps_of(own, act);
-      for (int w = 0; w < 3; ++w) {
-        while (act[w]) {
-          const int s = 32 * w + __ffs(act[w]) - 1;
-          act[w] &= act[w] - 1;
-          refresh();
-          const int r = s - 2 * lane;  // block row this lane visits at step s
-          if (static_cast<unsigned>(r) < static_cast<unsigned>(bh) && lane < bw && ((own >> (r + 1)) & 1ull) &&
-              visit(r))
-            rep1 |= 1ull << (r + 1);
-          __syncwarp();
-        }
+    // the first step at or after t with a visit to make, over the warp (INT_MAX: none)
+    auto next_step = [&](int t) -> int {
+      const uint64_t dd = lane < bw ? own & dirty & rows : 0ull;
+      int n = 0x7FFFFFFF;
+      if (dd & reached(t)) n = t;                                 // visited within 4 steps
+      else if (dd) n = x2 + __ffsll(static_cast<long long>(dd)) - 2;  // its first visit
+      return __reduce_min_sync(0xffffffffu, n);
+    };
+    for (int t = next_step(0); t != 0x7FFFFFFF; t = next_step(t + 1)) {
+      const int b = t - x2;
+      // damaged, dirty rows of this lane's column visited at step t: y = b - 4p, p >= 0
+      uint64_t cand = lane < bw && b >= 0 ? own & dirty & reached(t) & (0x2222222222222222ull << (b & 3)) : 0ull;
+      uint64_t mine = 0;
+      while (cand) {
+        const int j = __ffsll(static_cast<long long>(cand)) - 1;  // frame row; block row j - 1
+        cand &= cand - 1;
+        dirty &= ~(1ull << j);
+        if (visit(j - 1)) mine |= 1ull << j;
       }
-    }
-    // ---- later passes, while one repairs something.  A damaged pixel whose neighbourhood
-    // has not changed since it last failed the test fails it again, so a visit only checks
-    // "dirty" pixels: those next to a pixel repaired since their last check (after the
-    // first pass: next to any pixel it repaired).  The result is the same as visiting
-    // every damaged pixel; the work follows the repair front.
-    bool more = __any_sync(0xffffffffu, rep1 != 0) && __any_sync(0xffffffffu, lane < bw && (own & rows) != 0);
-    if (more) {
-      const uint64_t rl = __shfl_up_sync(0xffffffffu, rep1, 1), rr = __shfl_down_sync(0xffffffffu, rep1, 1);
-      const uint64_t near = rep1 | (lane > 0 ? rl : 0ull) | (lane < bw - 1 ? rr : 0ull);
-      uint64_t dirty = (near | (near << 1) | (near >> 1)) & own & rows;
-      refresh();
-      while (more) {
-        uint32_t act[3];
-        steps_of(own & dirty, act);
-        bool fixed = false;
-        for (int w = 0; w < 3; ++w) {
-          while (act[w]) {
-            const int s = 32 * w + __ffs(act[w]) - 1;
-            act[w] &= act[w] - 1;
-            const int r = s - 2 * lane;
-            const bool cand = static_cast<unsigned>(r) < static_cast<unsigned>(bh) && lane < bw &&
-                              (((own & dirty) >> (r + 1)) & 1ull);
-            bool rep = false;
-            if (cand) {
-              dirty &= ~(1ull << (r + 1));
-              rep = visit(r);
-            }
-            __syncwarp();
-            if (__any_sync(0xffffffffu, rep)) {
-              // new neighbour columns; their damaged neighbours (and this column's) become dirty
-              const uint64_t ol = lm, orr = rm;
-              refresh();
-              const uint64_t gone = (ol & ~lm) | (orr & ~rm) | (rep ? 1ull << (r + 1) : 0ull);
-              dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
-              fixed = true;
-              // a repair at step s can make pixels later in this pass dirty only at steps
-              // s + 1 (the next row of its column) .. s + 3 (the next column's three rows);
-              // those steps are visited (a step with no dirty damaged pixel does nothing)
-#pragma unroll
-              for (int k = 1; k <= 3; ++k)
-                if (s + k < 96) act[(s + k) >> 5] |= 1u << ((s + k) & 31);
-            }
-          }
-        }
-        more = fixed && __any_sync(0xffffffffu, lane < bw && (own & rows) != 0);
+      __syncwarp();
+      if (__any_sync(0xffffffffu, mine != 0)) {
+        // new neighbour columns; the damaged neighbours of every repair become dirty
+        const uint64_t ol = lm, orr = rm;
+        refresh();
+        const uint64_t gone = (ol & ~lm) | (orr & ~rm) | mine;
+        dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
       }
     }
     // ---- repaired pixels back into the view
