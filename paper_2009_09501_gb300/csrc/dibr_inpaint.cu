@@ -26,9 +26,8 @@ namespace {
 
 constexpr int kMaxBlock = 32;
 constexpr int kStride = kMaxBlock + 2;  // cells per row of a block's colour frame
-constexpr int kBlocksPerCta = 1;        // image blocks per CTA; one warp per block and view
-// (one block per CTA: a heavily damaged block holds only its own two warps' slot, not the
-// slots of lighter blocks that finished long before it)
+// One warp per CTA, one image block per warp; the warp takes the block's two views in turn
+// (a finished block frees its slot at once; no warp waits for another)
 
 // floor(v / (2n)) for v < 4096 and n = 2..8 as (v * ceil(65536 / 2n)) >> 16 (exact over that
 // range); index n.
@@ -40,12 +39,10 @@ __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
   p[2] = static_cast<uint8_t>(c >> 16);
 }
 
-__global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
-  __shared__ uint32_t cells[kBlocksPerCta][2][kStride * kStride];
-  __shared__ uint64_t repaired[kBlocksPerCta][2][kMaxBlock];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q = warp >> 1, v = warp & 1;
-  const int blk = blockIdx.x * kBlocksPerCta + q;
+__global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
+  __shared__ uint32_t cell[kStride * kStride];
+  const int lane = threadIdx.x;
+  const int blk = blockIdx.x;
   const int B = a.block, W = a.W, H = a.H;
   int bx0 = 0, by0 = 0, bw = 0, bh = 0;
   if (blk < a.nblocks) {
@@ -69,12 +66,9 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
     bw = min(B, W - bx0);
     bh = min(B, H - by0);
   }
-  uint8_t *view = a.view[v];
-  const uint32_t vbit = 1u << v;
-  uint32_t *cell = cells[q][v];
-
-  // ---- this view's holes inside the block (lane x: column x), every row's load in flight
-  uint64_t own = 0;
+  // ---- the holes of both views inside the block (lane x: column x), every row's load in
+  // flight
+  uint64_t own_l = 0, own_r = 0;
   {
     // (addresses of lanes and rows outside the block are clamped to the block's corner)
     const uint8_t *hp = a.holes + static_cast<int64_t>(by0) * a.holes_pitch + bx0 + (lane < bw ? lane : 0);
@@ -86,12 +80,20 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
       hb[r] = in ? v8 : 0u;
     }
 #pragma unroll
-    for (int r = 0; r < kMaxBlock; ++r)
-      if (hb[r] & vbit) own |= 2ull << r;
+    for (int r = 0; r < kMaxBlock; ++r) {
+      if (hb[r] & 1u) own_l |= 2ull << r;
+      if (hb[r] & 2u) own_r |= 2ull << r;
+    }
   }
-  const bool work = __any_sync(0xffffffffu, own != 0);
+  uint64_t rep_l = 0, rep_r = 0;  // per view, the repaired frame rows of this lane's column
+#pragma unroll 1
+  for (int v = 0; v < 2; ++v) {
+  uint8_t *view = a.view[v];
+  const uint32_t vbit = 1u << v;
+  uint64_t own = v ? own_r : own_l;
+  if (!__any_sync(0xffffffffu, own != 0)) continue;
   uint64_t own0 = own;
-  if (work) {
+  {
     // ---- colours of the block and its one-pixel frame, damage flags of the frame
     // (pixels outside the image count as damaged); eight rows of loads in flight at a time
     uint64_t col_a = 0, col_b = 0;  // flags of frame columns lane and lane + 32
@@ -232,19 +234,21 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
       store_rgb(view + static_cast<int64_t>(by0 + j - 1) * a.pitch + 3 * static_cast<int64_t>(bx0 + lane),
                 cell[j * kStride + lane + 1]);
     }
-    repaired[q][v][lane] = rep;
-  } else {
-    repaired[q][v][lane] = 0ull;
+    if (v) rep_r = rep;
+    else rep_l = rep;
   }
-  __syncthreads();  // both views of every block of this CTA are final in memory
+  __syncwarp();  // the frame of the next view goes into the same cells
+  }
+  __syncwarp();  // both views are final in memory for every lane
 
   // ---- formatted outputs where a view changed
-  const uint64_t rl = repaired[q][0][lane], rr = repaired[q][1][lane];
-  const uint64_t mine = v == 0 ? rl : rr;
-  const uint64_t pair = mine | __shfl_down_sync(0xffffffffu, mine, 1);  // rows where x or x + 1 changed
+  const uint64_t rl = rep_l, rr = rep_r;
+  // rows where x or x + 1 changed, per view
+  const uint64_t pair_l = rl | __shfl_down_sync(0xffffffffu, rl, 1);
+  const uint64_t pair_r = rr | __shfl_down_sync(0xffffffffu, rr, 1);
   if (lane < bw) {
     const int x = bx0 + lane;
-    if (v == 0 && a.ana) {
+    if (a.ana) {
       uint64_t m = rl | rr;
       while (m) {
         const int j = __ffsll(static_cast<long long>(m)) - 1;
@@ -256,9 +260,9 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
         d[2] = a.view[1][o + 2];
       }
     }
-    if (a.hsbs && (lane & 1) == 0) {
-      // pairs (x, x + 1) of this view; blocks start at even columns and have even widths
-      uint64_t m = pair;
+    for (int v = 0; a.hsbs && (lane & 1) == 0 && v < 2; ++v) {
+      // pairs (x, x + 1) of each view; blocks start at even columns and have even widths
+      uint64_t m = v ? pair_r : pair_l;
       const uint8_t *src = a.view[v];
       while (m) {
         const int j = __ffsll(static_cast<long long>(m)) - 1;
@@ -276,8 +280,7 @@ __global__ void __launch_bounds__(32 * 2 * kBlocksPerCta) inpaint_kernel(const _
 
 cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st) {
   if (a.nblocks <= 0) return cudaSuccess;
-  const int grid = (a.nblocks + kBlocksPerCta - 1) / kBlocksPerCta;
-  inpaint_kernel<<<grid, 32 * 2 * kBlocksPerCta, 0, st>>>(a);
+  inpaint_kernel<<<a.nblocks, 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
