@@ -66,80 +66,98 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
     bw = min(B, W - bx0);
     bh = min(B, H - by0);
   }
-  // ---- the holes of both views inside the block (lane x: column x), every row's load in
-  // flight
-  uint64_t own_l = 0, own_r = 0;
+  // ---- damage flags, both views (bit j = frame row j, block row j - 1; pixels outside the
+  // image count as damaged): of this lane's own column (lane x < bw: image column bx0 + x)
+  // over the frame rows 0 .. bh + 1, and of the halo columns bx0 - 1 and bx0 + bw, whose
+  // frame row j is read by lane j (rows 32 and 33 by lanes 0 and 1) and gathered by ballot.
+  // Every load in flight at once.
+  const int x = bx0 + lane;
+  const bool col = lane < bw;
+  uint64_t fl0 = 0, fl1 = 0;
   {
-    // (addresses of lanes and rows outside the block are clamped to the block's corner)
-    const uint8_t *hp = a.holes + static_cast<int64_t>(by0) * a.holes_pitch + bx0 + (lane < bw ? lane : 0);
-    uint32_t hb[kMaxBlock];
+    uint32_t hb[kMaxBlock + 2];
 #pragma unroll
-    for (int r = 0; r < kMaxBlock; ++r) {
-      const bool in = lane < bw && r < bh;
-      const uint32_t v8 = hp[static_cast<int64_t>(r < bh ? r : 0) * a.holes_pitch];
-      hb[r] = in ? v8 : 0u;
+    for (int j = 0; j < kMaxBlock + 2; ++j) {
+      const int y = by0 - 1 + j;
+      const bool frame = col && j < bh + 2, in = frame && y >= 0 && y < H;
+      const uint32_t h8 = a.holes[static_cast<int64_t>(in ? y : by0) * a.holes_pitch + (col ? x : bx0)];
+      hb[j] = in ? h8 : frame ? 3u : 0u;
     }
 #pragma unroll
-    for (int r = 0; r < kMaxBlock; ++r) {
-      if (hb[r] & 1u) own_l |= 2ull << r;
-      if (hb[r] & 2u) own_r |= 2ull << r;
+    for (int j = 0; j < kMaxBlock + 2; ++j) {
+      if (hb[j] & 1u) fl0 |= 1ull << j;
+      if (hb[j] & 2u) fl1 |= 1ull << j;
     }
   }
-  uint64_t rep_l = 0, rep_r = 0;  // per view, the repaired frame rows of this lane's column
+  // halo pixels of this lane: frame rows hj[k], left (column bx0 - 1) and right (bx0 + bw)
+  const int hj[2] = {lane, 32 + lane};
+  uint32_t hl8[2], hr8[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int j = hj[k], y = by0 - 1 + j;
+    const bool frame = j < bh + 2, rin = frame && y >= 0 && y < H;
+    const bool lin = rin && bx0 > 0, rinr = rin && bx0 + bw < W;
+    const int64_t yy = rin ? y : by0;
+    const uint32_t l8 = a.holes[yy * a.holes_pitch + (lin ? bx0 - 1 : bx0)];
+    const uint32_t r8 = a.holes[yy * a.holes_pitch + (rinr ? bx0 + bw : bx0)];
+    hl8[k] = lin ? l8 : frame ? 3u : 0u;
+    hr8[k] = rinr ? r8 : frame ? 3u : 0u;
+  }
+  const uint64_t rows = ((1ull << bh) - 1ull) << 1;  // the block's own rows in a column mask
 #pragma unroll 1
   for (int v = 0; v < 2; ++v) {
   uint8_t *view = a.view[v];
-  const uint32_t vbit = 1u << v;
-  uint64_t own = v ? own_r : own_l;
-  if (!__any_sync(0xffffffffu, own != 0)) continue;
-  uint64_t own0 = own;
+  uint64_t own = col ? (v ? fl1 : fl0) : ~0ull;
+  if (!__any_sync(0xffffffffu, col && (own & rows) != 0)) continue;
+  const uint64_t own0 = own;
+  const uint64_t halo_l = __ballot_sync(0xffffffffu, (hl8[0] >> v) & 1u) |
+                          (static_cast<uint64_t>(__ballot_sync(0xffffffffu, (hl8[1] >> v) & 1u) & 3u) << 32);
+  const uint64_t halo_r = __ballot_sync(0xffffffffu, (hr8[0] >> v) & 1u) |
+                          (static_cast<uint64_t>(__ballot_sync(0xffffffffu, (hr8[1] >> v) & 1u) & 3u) << 32);
   {
-    // ---- colours of the block and its one-pixel frame, damage flags of the frame
-    // (pixels outside the image count as damaged); eight rows of loads in flight at a time
-    uint64_t col_a = 0, col_b = 0;  // flags of frame columns lane and lane + 32
-    for (int i = lane; i < bw + 2; i += 32) {
-      const int x = bx0 - 1 + i;
-      const bool xin = x >= 0 && x < W;
-      uint64_t flags = 0;
-      for (int j0 = 0; j0 < bh + 2; j0 += 8) {
-        uint32_t hv[8], c0[8], c1[8], c2[8];
+    // ---- colours of the frame into the cells: undamaged pixels their colour, damaged ones
+    // 0; kBatch rows of loads in flight at a time
+    constexpr int kBatch = 10;
+    for (int j0 = 0; j0 < bh + 2; j0 += kBatch) {
+      uint32_t c0[kBatch], c1[kBatch], c2[kBatch];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = j0 + t, y = by0 - 1 + j;
-          const bool in = xin && j < bh + 2 && y >= 0 && y < H;
-          const int64_t yy = in ? y : by0, xx = in ? x : bx0;  // pixels outside: read (bx0, by0), unused
-          const uint8_t *px = view + yy * a.pitch + 3 * xx;
-          const uint32_t h8 = a.holes[yy * a.holes_pitch + xx];
-          hv[t] = in ? h8 : 0xFFu;
+      for (int t = 0; t < kBatch; ++t) {
+        const int j = j0 + t;
+        const bool need = col && j < bh + 2 && !((own >> j) & 1ull);
+        c0[t] = c1[t] = c2[t] = 0u;
+        if (need) {
+          const uint8_t *px = view + static_cast<int64_t>(by0 - 1 + j) * a.pitch + 3 * static_cast<int64_t>(x);
           c0[t] = px[0];
           c1[t] = px[1];
           c2[t] = px[2];
         }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int j = j0 + t;
-          if (j >= bh + 2) break;
-          const bool bad = (hv[t] & vbit) != 0;
-          cell[j * kStride + i] = bad ? 0u : (c0[t] | (c1[t] << 8) | (c2[t] << 16));
-          if (bad) flags |= 1ull << j;
-        }
       }
-      if (i < 32) col_a = flags;
-      else col_b = flags;
+#pragma unroll
+      for (int t = 0; t < kBatch; ++t) {
+        const int j = j0 + t;
+        if (col && j < bh + 2) cell[j * kStride + lane + 1] = c0[t] | (c1[t] << 8) | (c2[t] << 16);
+      }
     }
-    // lane x (< bw) owns frame column x + 1; the frame columns 0 and bw + 1 are the halo
-    const uint64_t next_a = __shfl_sync(0xffffffffu, col_a, (lane + 1) & 31);
-    const uint64_t first_b = __shfl_sync(0xffffffffu, col_b, 0);
-    own = lane < bw ? (lane < 31 ? next_a : first_b) : ~0ull;
-    own0 = own;
-    const uint64_t halo_l = __shfl_sync(0xffffffffu, col_a, 0);
-    const int hr = bw + 1;
-    const uint64_t hr_a = __shfl_sync(0xffffffffu, col_a, hr & 31);
-    const uint64_t hr_b = __shfl_sync(0xffffffffu, col_b, hr & 31);
-    const uint64_t halo_r = hr < 32 ? hr_a : hr_b;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int j = hj[k];
+      if (j < bh + 2) {
+        const int64_t ro = static_cast<int64_t>(by0 - 1 + j) * a.pitch;
+        uint32_t cl = 0u, cr = 0u;
+        if (!((halo_l >> j) & 1ull)) {
+          const uint8_t *px = view + ro + 3 * static_cast<int64_t>(bx0 - 1);
+          cl = px[0] | (px[1] << 8) | (px[2] << 16);
+        }
+        if (!((halo_r >> j) & 1ull)) {
+          const uint8_t *px = view + ro + 3 * static_cast<int64_t>(bx0 + bw);
+          cr = px[0] | (px[1] << 8) | (px[2] << 16);
+        }
+        cell[j * kStride] = cl;
+        cell[j * kStride + bw + 1] = cr;
+      }
+    }
     __syncwarp();
 
-    const uint64_t rows = ((1ull << bh) - 1ull) << 1;  // the block's own rows in a column mask
     uint64_t lm = 0, rm = 0;  // damage flags of the neighbouring columns
     auto refresh = [&]() {
       lm = __shfl_up_sync(0xffffffffu, own, 1);
@@ -225,54 +243,46 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
         dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
       }
     }
-    // ---- repaired pixels back into the view
-    const uint64_t rep = lane < bw ? (own0 & ~own & rows) : 0ull;
+    // ---- repaired pixels back into the view, and the formatted outputs where it changed:
+    // the anaglyph takes red from the left view and green, blue from the right one; a
+    // half side-by-side pixel is the rounded-up mean of the pair (x, x + 1) of its view
+    // (blocks start at even columns and have even widths), from the cells, or from the view
+    // for a pixel left damaged (it keeps the colour of the row fill)
+    const uint64_t rep = col ? (own0 & ~own & rows) : 0ull;
+    const uint64_t pair = rep | __shfl_down_sync(0xffffffffu, rep, 1);
+    const uint64_t own_n = __shfl_down_sync(0xffffffffu, own, 1);
     uint64_t left = rep;
     while (left) {
-      const int j = __ffsll(static_cast<long long>(left)) - 1;  // frame row; block row j - 1
+      const int j = __ffsll(static_cast<long long>(left)) - 1;
       left &= left - 1;
-      store_rgb(view + static_cast<int64_t>(by0 + j - 1) * a.pitch + 3 * static_cast<int64_t>(bx0 + lane),
-                cell[j * kStride + lane + 1]);
+      const int64_t y = by0 + j - 1;
+      const uint32_t c = cell[j * kStride + lane + 1];
+      store_rgb(view + y * a.pitch + 3 * static_cast<int64_t>(x), c);
+      if (a.ana) {
+        uint8_t *d = a.ana + y * a.out_pitch + 3 * static_cast<int64_t>(x);
+        if (v == 0) {
+          d[0] = static_cast<uint8_t>(c);
+        } else {
+          d[1] = static_cast<uint8_t>(c >> 8);
+          d[2] = static_cast<uint8_t>(c >> 16);
+        }
+      }
     }
-    if (v) rep_r = rep;
-    else rep_l = rep;
+    if (a.hsbs && col && (lane & 1) == 0) {
+      uint64_t m = pair;
+      while (m) {
+        const int j = __ffsll(static_cast<long long>(m)) - 1;
+        m &= m - 1;
+        const int64_t y = by0 + j - 1;
+        const uint8_t *p = view + y * a.pitch + 3 * static_cast<int64_t>(x);
+        const uint32_t ca = ((own >> j) & 1ull) ? (p[0] | (p[1] << 8) | (p[2] << 16)) : cell[j * kStride + lane + 1];
+        const uint32_t cb = ((own_n >> j) & 1ull) ? (p[3] | (p[4] << 8) | (p[5] << 16)) : cell[j * kStride + lane + 2];
+        const uint32_t mean = (ca | cb) - (((ca ^ cb) >> 1) & 0x7F7F7F7Fu);  // per byte (a + b + 1) >> 1
+        store_rgb(a.hsbs + y * a.out_pitch + 3 * static_cast<int64_t>((v ? W / 2 : 0) + x / 2), mean);
+      }
+    }
   }
   __syncwarp();  // the frame of the next view goes into the same cells
-  }
-  __syncwarp();  // both views are final in memory for every lane
-
-  // ---- formatted outputs where a view changed
-  const uint64_t rl = rep_l, rr = rep_r;
-  // rows where x or x + 1 changed, per view
-  const uint64_t pair_l = rl | __shfl_down_sync(0xffffffffu, rl, 1);
-  const uint64_t pair_r = rr | __shfl_down_sync(0xffffffffu, rr, 1);
-  if (lane < bw) {
-    const int x = bx0 + lane;
-    if (a.ana) {
-      uint64_t m = rl | rr;
-      while (m) {
-        const int j = __ffsll(static_cast<long long>(m)) - 1;
-        m &= m - 1;
-        const int64_t o = static_cast<int64_t>(by0 + j - 1) * a.pitch + 3 * static_cast<int64_t>(x);
-        uint8_t *d = a.ana + static_cast<int64_t>(by0 + j - 1) * a.out_pitch + 3 * static_cast<int64_t>(x);
-        d[0] = a.view[0][o];
-        d[1] = a.view[1][o + 1];
-        d[2] = a.view[1][o + 2];
-      }
-    }
-    for (int v = 0; a.hsbs && (lane & 1) == 0 && v < 2; ++v) {
-      // pairs (x, x + 1) of each view; blocks start at even columns and have even widths
-      uint64_t m = v ? pair_r : pair_l;
-      const uint8_t *src = a.view[v];
-      while (m) {
-        const int j = __ffsll(static_cast<long long>(m)) - 1;
-        m &= m - 1;
-        const int y = by0 + j - 1;
-        const uint8_t *p = src + static_cast<int64_t>(y) * a.pitch + 3 * static_cast<int64_t>(x);
-        uint8_t *d = a.hsbs + static_cast<int64_t>(y) * a.out_pitch + 3 * static_cast<int64_t>((v ? W / 2 : 0) + x / 2);
-        for (int c = 0; c < 3; ++c) d[c] = static_cast<uint8_t>((p[c] + p[3 + c] + 1) >> 1);
-      }
-    }
   }
 }
 
