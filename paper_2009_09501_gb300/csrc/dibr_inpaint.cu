@@ -11,9 +11,9 @@
 // a block whose repairs creep one column per pass (the undamaged side to the right of a
 // wide hole) takes about 2B + B + 4 x passes steps instead of B steps per pass.
 //
-// The damage flags of a column live in a 64-bit register of its lane (bit j = block row
-// j - 1, with the rows above and below the block at bits 0 and B + 1); a lane reads its
-// neighbours' columns with shuffles at the step it needs them.  Colours live in shared
+// The damage flags of a column live in a 32-bit register of its lane (bit y = block row
+// y; the rows above and below the block never change and are kept apart); a lane reads its
+// neighbours' columns with shuffles after a step that repaired something.  Colours live in shared
 // memory with a one-pixel frame around the block.  Pixels outside the block are read as
 // the band kernel left them (they are never written by this block, and their damage
 // flags come from the holes map, which nothing changes), so blocks are independent.
@@ -103,13 +103,24 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
     hl8[k] = lin ? l8 : frame ? 3u : 0u;
     hr8[k] = rinr ? r8 : frame ? 3u : 0u;
   }
-  const uint64_t rows = ((1ull << bh) - 1ull) << 1;  // the block's own rows in a column mask
+  const uint32_t rows = bh >= 32 ? 0xFFFFFFFFu : (1u << bh) - 1u;  // the block's rows (bit y = row y)
+  // a column's damage in the frame rows (bit 0: the row above the block, bit 1: the row below)
+  auto frame_bits = [&](uint64_t f) -> uint32_t {
+    return static_cast<uint32_t>(f & 1ull) | (static_cast<uint32_t>((f >> (bh + 1)) & 1ull) << 1);
+  };
+  // ... and as a mask of frame rows, to be OR-ed with a column's block rows shifted up by one
+  auto frame_mask = [&](uint32_t fb) -> uint64_t {
+    return static_cast<uint64_t>(fb & 1u) | (static_cast<uint64_t>(fb >> 1) << (bh + 1));
+  };
 #pragma unroll 1
   for (int v = 0; v < 2; ++v) {
   uint8_t *view = a.view[v];
-  uint64_t own = col ? (v ? fl1 : fl0) : ~0ull;
-  if (!__any_sync(0xffffffffu, col && (own & rows) != 0)) continue;
-  const uint64_t own0 = own;
+  const uint64_t fl = col ? (v ? fl1 : fl0) : ~0ull;  // frame rows
+  // damaged block rows of this lane's column (bit y = block row y); every row beyond a
+  // real column counts as damaged
+  uint32_t own = col ? static_cast<uint32_t>(fl >> 1) & rows : 0xFFFFFFFFu;
+  if (!__any_sync(0xffffffffu, col && own != 0u)) continue;
+  const uint32_t own0 = own;
   const uint64_t halo_l = __ballot_sync(0xffffffffu, (hl8[0] >> v) & 1u) |
                           (static_cast<uint64_t>(__ballot_sync(0xffffffffu, (hl8[1] >> v) & 1u) & 3u) << 32);
   const uint64_t halo_r = __ballot_sync(0xffffffffu, (hr8[0] >> v) & 1u) |
@@ -123,7 +134,7 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
 #pragma unroll
       for (int t = 0; t < kBatch; ++t) {
         const int j = j0 + t;
-        const bool need = col && j < bh + 2 && !((own >> j) & 1ull);
+        const bool need = col && j < bh + 2 && !((fl >> j) & 1ull);
         c0[t] = c1[t] = c2[t] = 0u;
         if (need) {
           const uint8_t *px = view + static_cast<int64_t>(by0 - 1 + j) * a.pitch + 3 * static_cast<int64_t>(x);
@@ -158,20 +169,29 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
     }
     __syncwarp();
 
-    uint64_t lm = 0, rm = 0;  // damage flags of the neighbouring columns
+    // the neighbouring columns' damage (block rows, from their lanes or the halo) and the
+    // frame rows of all three columns (constant)
+    const uint32_t fo = col ? frame_bits(fl) : 3u;
+    uint32_t fl_l = __shfl_up_sync(0xffffffffu, fo, 1), fl_r = __shfl_down_sync(0xffffffffu, fo, 1);
+    if (lane == 0) fl_l = frame_bits(halo_l);
+    if (lane == bw - 1) fl_r = frame_bits(halo_r);
+    const uint64_t F_l = frame_mask(fl_l), F_o = frame_mask(fo), F_r = frame_mask(fl_r);
+    const uint32_t hl = static_cast<uint32_t>(halo_l >> 1) & rows, hr = static_cast<uint32_t>(halo_r >> 1) & rows;
+    uint32_t lm = 0, rm = 0;
     auto refresh = [&]() {
       lm = __shfl_up_sync(0xffffffffu, own, 1);
       rm = __shfl_down_sync(0xffffffffu, own, 1);
-      if (lane == 0) lm = halo_l;
-      if (lane == bw - 1) rm = halo_r;
+      if (lane == 0) lm = hl;
+      if (lane == bw - 1) rm = hr;
     };
     // The visit of damaged block row r of this lane's column: with two or more undamaged
     // neighbours the pixel takes their mean colour and is no longer damaged.
     auto visit = [&](int r) -> bool {
-      // frame rows r, r + 1 (the pixel's own), r + 2 of the three columns
-      const uint32_t bl = static_cast<uint32_t>(lm >> r) & 7u;
-      const uint32_t bo = static_cast<uint32_t>(own >> r) & 5u;
-      const uint32_t br = static_cast<uint32_t>(rm >> r) & 7u;
+      // rows r - 1, r (the pixel's own), r + 1 of the three columns (row -1 and row bh are
+      // the frame rows: bit k of a column mask shifted up by one is frame row k)
+      const uint32_t bl = static_cast<uint32_t>(((static_cast<uint64_t>(lm) << 1) | F_l) >> r) & 7u;
+      const uint32_t bo = static_cast<uint32_t>(((static_cast<uint64_t>(own) << 1) | F_o) >> r) & 5u;
+      const uint32_t br = static_cast<uint32_t>(((static_cast<uint64_t>(rm) << 1) | F_r) >> r) & 7u;
       const int n = 8 - __popc(bl) - __popc(bo) - __popc(br);
       if (n < 2) return false;
       // A damaged cell holds 0 until it is repaired (and then its flag is cleared with the
@@ -190,7 +210,7 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
       const uint32_t mr = ((2u * (srb & 0xFFFFu) + n) * rc) >> 16, mb = ((2u * (srb >> 16) + n) * rc) >> 16;
       const uint32_t mg = ((2u * sg + n) * rc) >> 16;
       cell[(r + 1) * kStride + lane + 1] = mr | (mg << 8) | (mb << 16);
-      own &= ~(1ull << (r + 1));
+      own &= ~(1u << r);
       return true;
     };
     // ---- the passes, pipelined.  Pass p visits block pixel (x, y) at step 2x + y + 4p.
@@ -207,39 +227,39 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
     // repair since their last visit); when no damaged pixel is dirty nothing can change any
     // more, which is where the figure's loop ends too (a pass that repairs nothing).  Steps
     // at which no lane has a dirty pixel to visit are skipped.
-    uint64_t dirty = own & rows;
+    uint32_t dirty = own & rows;
     refresh();
     const int x2 = 2 * lane;
-    // frame rows j (block row j - 1) that lane x has reached by step t: j - 1 <= t - 2x
-    auto reached = [&](int t) -> uint64_t {
+    // block rows y that lane x has reached by step t: y <= t - 2x
+    auto reached = [&](int t) -> uint32_t {
       const int b = t - x2;
-      return b < 0 ? 0ull : b >= 32 ? ~0ull : (4ull << b) - 1ull;
+      return b < 0 ? 0u : b >= 31 ? 0xFFFFFFFFu : (2u << b) - 1u;
     };
     // the first step at or after t with a visit to make, over the warp (INT_MAX: none)
     auto next_step = [&](int t) -> int {
-      const uint64_t dd = lane < bw ? own & dirty & rows : 0ull;
+      const uint32_t dd = col ? own & dirty : 0u;
       int n = 0x7FFFFFFF;
-      if (dd & reached(t)) n = t;                                 // visited within 4 steps
-      else if (dd) n = x2 + __ffsll(static_cast<long long>(dd)) - 2;  // its first visit
+      if (dd & reached(t)) n = t;                  // visited within 4 steps
+      else if (dd) n = x2 + __ffs(dd) - 1;         // its first visit
       return __reduce_min_sync(0xffffffffu, n);
     };
     for (int t = next_step(0); t != 0x7FFFFFFF; t = next_step(t + 1)) {
       const int b = t - x2;
       // damaged, dirty rows of this lane's column visited at step t: y = b - 4p, p >= 0
-      uint64_t cand = lane < bw && b >= 0 ? own & dirty & reached(t) & (0x2222222222222222ull << (b & 3)) : 0ull;
-      uint64_t mine = 0;
+      uint32_t cand = col && b >= 0 ? own & dirty & reached(t) & (0x11111111u << (b & 3)) : 0u;
+      uint32_t mine = 0;
       while (cand) {
-        const int j = __ffsll(static_cast<long long>(cand)) - 1;  // frame row; block row j - 1
+        const int y = __ffs(cand) - 1;
         cand &= cand - 1;
-        dirty &= ~(1ull << j);
-        if (visit(j - 1)) mine |= 1ull << j;
+        dirty &= ~(1u << y);
+        if (visit(y)) mine |= 1u << y;
       }
       __syncwarp();
-      if (__any_sync(0xffffffffu, mine != 0)) {
+      if (__any_sync(0xffffffffu, mine != 0u)) {
         // new neighbour columns; the damaged neighbours of every repair become dirty
-        const uint64_t ol = lm, orr = rm;
+        const uint32_t ol = lm, orr = rm;
         refresh();
-        const uint64_t gone = (ol & ~lm) | (orr & ~rm) | mine;
+        const uint32_t gone = (ol & ~lm) | (orr & ~rm) | mine;
         dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
       }
     }
@@ -248,18 +268,18 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
     // half side-by-side pixel is the rounded-up mean of the pair (x, x + 1) of its view
     // (blocks start at even columns and have even widths), from the cells, or from the view
     // for a pixel left damaged (it keeps the colour of the row fill)
-    const uint64_t rep = col ? (own0 & ~own & rows) : 0ull;
-    const uint64_t pair = rep | __shfl_down_sync(0xffffffffu, rep, 1);
-    const uint64_t own_n = __shfl_down_sync(0xffffffffu, own, 1);
-    uint64_t left = rep;
+    const uint32_t rep = col ? (own0 & ~own & rows) : 0u;
+    const uint32_t pair = rep | __shfl_down_sync(0xffffffffu, rep, 1);
+    const uint32_t own_n = __shfl_down_sync(0xffffffffu, own, 1);
+    uint32_t left = rep;
     while (left) {
-      const int j = __ffsll(static_cast<long long>(left)) - 1;
+      const int y = __ffs(left) - 1;  // block row; frame row y + 1
       left &= left - 1;
-      const int64_t y = by0 + j - 1;
-      const uint32_t c = cell[j * kStride + lane + 1];
-      store_rgb(view + y * a.pitch + 3 * static_cast<int64_t>(x), c);
+      const int64_t iy = by0 + y;
+      const uint32_t c = cell[(y + 1) * kStride + lane + 1];
+      store_rgb(view + iy * a.pitch + 3 * static_cast<int64_t>(x), c);
       if (a.ana) {
-        uint8_t *d = a.ana + y * a.out_pitch + 3 * static_cast<int64_t>(x);
+        uint8_t *d = a.ana + iy * a.out_pitch + 3 * static_cast<int64_t>(x);
         if (v == 0) {
           d[0] = static_cast<uint8_t>(c);
         } else {
@@ -269,16 +289,16 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
       }
     }
     if (a.hsbs && col && (lane & 1) == 0) {
-      uint64_t m = pair;
+      uint32_t m = pair;
       while (m) {
-        const int j = __ffsll(static_cast<long long>(m)) - 1;
+        const int y = __ffs(m) - 1;
         m &= m - 1;
-        const int64_t y = by0 + j - 1;
-        const uint8_t *p = view + y * a.pitch + 3 * static_cast<int64_t>(x);
-        const uint32_t ca = ((own >> j) & 1ull) ? (p[0] | (p[1] << 8) | (p[2] << 16)) : cell[j * kStride + lane + 1];
-        const uint32_t cb = ((own_n >> j) & 1ull) ? (p[3] | (p[4] << 8) | (p[5] << 16)) : cell[j * kStride + lane + 2];
+        const int64_t iy = by0 + y;
+        const uint8_t *p = view + iy * a.pitch + 3 * static_cast<int64_t>(x);
+        const uint32_t ca = ((own >> y) & 1u) ? (p[0] | (p[1] << 8) | (p[2] << 16)) : cell[(y + 1) * kStride + lane + 1];
+        const uint32_t cb = ((own_n >> y) & 1u) ? (p[3] | (p[4] << 8) | (p[5] << 16)) : cell[(y + 1) * kStride + lane + 2];
         const uint32_t mean = (ca | cb) - (((ca ^ cb) >> 1) & 0x7F7F7F7Fu);  // per byte (a + b + 1) >> 1
-        store_rgb(a.hsbs + y * a.out_pitch + 3 * static_cast<int64_t>((v ? W / 2 : 0) + x / 2), mean);
+        store_rgb(a.hsbs + iy * a.out_pitch + 3 * static_cast<int64_t>((v ? W / 2 : 0) + x / 2), mean);
       }
     }
   }
