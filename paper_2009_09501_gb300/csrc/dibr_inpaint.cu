@@ -255,13 +255,11 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
         if (visit(y)) mine |= 1u << y;
       }
       __syncwarp();
-      if (__any_sync(0xffffffffu, mine != 0u)) {
-        // new neighbour columns; the damaged neighbours of every repair become dirty
-        const uint32_t ol = lm, orr = rm;
-        refresh();
-        const uint32_t gone = (ol & ~lm) | (orr & ~rm) | mine;
-        dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
-      }
+      // new neighbour columns; the damaged neighbours of every repair become dirty
+      const uint32_t ol = lm, orr = rm;
+      refresh();
+      const uint32_t gone = (ol & ~lm) | (orr & ~rm) | mine;
+      dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
     }
     // ---- repaired pixels back into the view, and the formatted outputs where it changed:
     // the anaglyph takes red from the left view and green, blue from the right one; a
