@@ -8,13 +8,12 @@
 // the accumulation small next to the final half-integer decision.
 //
 // One CTA computes a 32 x 8 tile; the tile plus an r-pixel apron is staged in shared
-// memory once: the colour (RGB in the low three bytes) and the luminance (as a float).
-// Per tap: two shared loads, the squared colour distance exactly in two integer
-// instructions (per-byte absolute differences, then a byte dot product of that word
-// with itself), one FMA for the exponent (the spatial
-// part is a per-tap constant: the radius is a template parameter, so the taps unroll),
-// one exp2 on the special-function unit (the constants are pre-scaled by log2 e), and
-// two accumulations.  The integer-to-float conversion of the distance, which would share
+// memory once, one 8-byte cell per pixel: the colour (RGB in the low three bytes) and the
+// luminance (as a float).  Per tap: one shared load, the squared colour distance exactly
+// in two integer instructions (per-byte absolute differences, then a byte dot product of
+// that word with itself), one FMA for the exponent (the spatial part is a per-tap
+// constant: the radius is a template parameter, so the taps unroll), one exp2 on the
+// special-function unit (the constants are pre-scaled by log2 e), and two accumulations.  The integer-to-float conversion of the distance, which would share
 // the special-function unit's low rate, is an exact mantissa trick, so the exp2 is the
 // only such operation per tap.
 #include "dibr_internal.h"
@@ -54,8 +53,7 @@ __device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float yq, floa
 template <int R>
 __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
                                                        float as, float ar, uint8_t *__restrict__ D, int64_t dpitch) {
-  __shared__ uint32_t col[kTY + 2 * R][kTX + 2 * R];  // 0x00BBGGRR
-  __shared__ float lum[kTY + 2 * R][kTX + 2 * R];
+  __shared__ uint2 px[kTY + 2 * R][kTX + 2 * R];  // colour 0x00BBGGRR, luminance as float bits
   const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY;
   constexpr int ax = kTX + 2 * R, ay = kTY + 2 * R;
   for (int i = threadIdx.x; i < ax * ay; i += blockDim.x) {
@@ -69,15 +67,15 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
       c = r | (g << 8) | (b << 16);
       l = luma8x(r, g, b);
     }
-    col[ty][tx] = c;
-    lum[ty][tx] = static_cast<float>(l);
+    px[ty][tx] = make_uint2(c, __float_as_uint(static_cast<float>(l)));
   }
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const int x = bx + tx, y = by + ty;
   if (x >= W || y >= H) return;
-  const uint32_t cp = col[ty + R][tx + R];
-  const float yp = lum[ty + R][tx + R];
+  const uint2 pc = px[ty + R][tx + R];
+  const uint32_t cp = pc.x;
+  const float yp = __uint_as_float(pc.y);
   // exponents in base 2: w = 2^(-(s2 * as + d2 * ar) * log2 e)
   constexpr float kLog2e = 1.4426950408889634f;
   const float nas = -as * kLog2e, nar = -ar * kLog2e;
@@ -86,15 +84,17 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
 #pragma unroll
     for (int dy = -R; dy <= R; ++dy)
 #pragma unroll
-      for (int dx = -R; dx <= R; ++dx)
-        xbf_tap(cp, col[ty + R + dy][tx + R + dx], lum[ty + R + dy][tx + R + dx],
-                static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+      for (int dx = -R; dx <= R; ++dx) {
+        const uint2 q = px[ty + R + dy][tx + R + dx];
+        xbf_tap(cp, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+      }
   } else {  // the window clipped to the image
     const int x0 = max(-R, -x), x1 = min(R, W - 1 - x), y0 = max(-R, -y), y1 = min(R, H - 1 - y);
     for (int dy = y0; dy <= y1; ++dy)
-      for (int dx = x0; dx <= x1; ++dx)
-        xbf_tap(cp, col[ty + R + dy][tx + R + dx], lum[ty + R + dy][tx + R + dx],
-                static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+      for (int dx = x0; dx <= x1; ++dx) {
+        const uint2 q = px[ty + R + dy][tx + R + dx];
+        xbf_tap(cp, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+      }
   }
   const float q = floorf(num / den + 0.5f);
   const int v = static_cast<int>(yp) + static_cast<int>(q);
