@@ -632,8 +632,9 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         // the row's last, partial warp: columns from warp_hi on do not exist (their loads
         // read column warp_hi - 1, so that they stay in the row; their atomics are skipped)
         const uint32_t rs = smem_addr(rgbrow), dr = smem_addr(m.drow);
+        const int ng = (warp_hi - warp_lo + 127) >> 7;  // groups of 4 x 32 columns holding some
 #pragma unroll 1
-        for (int g = 0; g < kChunk / 4; ++g) {
+        for (int g = 0; g < ng; ++g) {
           uint32_t dv[4], cw[8];
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
