@@ -250,10 +250,13 @@ dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const di
  *                  2: it does not;
  *   rows_per_unit  rows per work unit of a batched launch (dibr_synthesize_batch and
  *                  the serving loop); automatic: one unit per SM slot when an image group
- *                  is small (one 4K frame: 8 rows), 32 rows otherwise.
+ *                  is small (one 4K frame: 8 rows), 32 rows otherwise;
+ *   host_bands     row bands of dibr_synthesize_image with host input and outputs (the
+ *                  bands' uploads, kernels and downloads overlap), 1..8; automatic: 4 from
+ *                  2048 rows, 2 from 512, else 1.
  * dibr_set_tuning() rejects out-of-range values with DIBR_E_INVALID. */
 typedef struct {
-    int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit;
+    int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit, host_bands;
 } dibr_tuning;
 
 dibr_status dibr_set_tuning(dibr_ctx *ctx, const dibr_tuning *t);

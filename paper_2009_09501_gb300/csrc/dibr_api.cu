@@ -560,7 +560,8 @@ dibr_status dibr_set_tuning(dibr_ctx *c, const dibr_tuning *t) {
   if (!c || !t) return DIBR_E_INVALID;
   if (t->ring_slots < 0 || t->ring_slots > kMaxRing || (t->ring_slots > 0 && t->ring_slots < 2) ||
       t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || t->load_mode < 0 || t->load_mode > 5 ||
-      t->l2_prefetch < 0 || t->l2_prefetch > 2 || t->rows_per_unit < 0 || t->rows_per_unit > 4096) {
+      t->l2_prefetch < 0 || t->l2_prefetch > 2 || t->rows_per_unit < 0 || t->rows_per_unit > 4096 ||
+      t->host_bands < 0 || t->host_bands > dibr_ctx::kMaxBands) {
     c->set_error("tuning value out of range");
     return DIBR_E_INVALID;
   }
@@ -672,8 +673,11 @@ dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params
   }
   for (int k = 0; k < bands; ++k) {
     const int y0 = band_row(k), y1 = band_row(k + 1);
-    // rows y0 - 2 .. y1 + 1 of the input: bands up to k + 1
-    cudaStreamWaitEvent(stream, ev_in[k + 1 < bands ? k + 1 : k], 0);
+    // rows y0 - 2 .. y1 + 1 of the input: the uploads up to the band holding row y1 + 1
+    // (they complete in order on one stream)
+    int kl = k;
+    while (kl + 1 < bands && band_row(kl + 1) <= std::min(y1 + 1, H - 1)) ++kl;
+    cudaStreamWaitEvent(stream, ev_in[kl], 0);
     a.row0 = y0;
     a.row1 = y1;
     a.grid = std::max(1, std::min(y1 - y0, slots));
@@ -725,7 +729,7 @@ dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params
   // row bands when both sides of the call are in host memory and every row band is
   // independent of the others' results (not with the 2-D fill or the cross-bilateral depth,
   // which need the whole frame first)
-  const int bands = H >= 2048 ? 4 : H >= 512 ? 2 : 1;
+  const int bands = tuning.host_bands > 0 ? std::min(tuning.host_bands, H) : H >= 2048 ? 4 : H >= 512 ? 2 : 1;
   if (bands > 1 && !img->on_device && !o->on_device && p->hole_fill == DIBR_FILL_ROW &&
       p->depth_rule != DIBR_DEPTH_LUMA_XBF)
     return synthesize_banded(img, p, o, bands);

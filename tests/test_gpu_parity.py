@@ -255,6 +255,23 @@ def test_host_buffers_row_bands(ctx, torch, oracle, W, H, P):
     assert_same(outs, ref, "banded %dx%d" % (W, H))
 
 
+@pytest.mark.parametrize("bands", [1, 2, 3, 5, 8])
+def test_host_buffers_band_counts(ctx, torch, oracle, bands):
+    # every band count of the blocking host-buffer path, down to bands of one or two rows
+    # (the 2-row halos then span two bands)
+    for W, H in [(333, 9), (640, 37)]:
+        img = scenes.Scene(W, H, seed=W + bands, n_objects=8).frame(0)
+        want = ("anaglyph", "left", "right", "depth")
+        outs = {n: np.zeros((H, W) if n in D.MAP_OUTPUTS else (H, W, 3), np.uint8) for n in want}
+        ctx.set_tuning(host_bands=bands)
+        try:
+            ctx.synthesize_image(np.ascontiguousarray(img), D.make_params(max_parallax=24, outputs=want), outs)
+        finally:
+            ctx.set_tuning(host_bands=0)
+        ref = oracle.dibr(img, oracle.params(max_parallax=24), want=want)
+        assert_same(outs, ref, "%d bands %dx%d" % (bands, W, H))
+
+
 def test_back_to_back_frames_overlap_only_when_independent(ctx, torch, oracle):
     # consecutive asynchronous frames on the context's own stream: disjoint buffers may
     # overlap on the GPU, a frame reading the previous frame's output must not
