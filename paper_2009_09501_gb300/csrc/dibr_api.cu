@@ -425,6 +425,9 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     ia.block = p->inpaint_block;
     ia.nbx = (W + ia.block - 1) / ia.block;
     ia.nblocks = ia.nbx * ((H + ia.block - 1) / ia.block);
+    if ((s = ensure(inpaint_order, sizeof(int32_t) * (static_cast<size_t>(ia.nblocks) + 3))) != DIBR_OK) return s;
+    ia.sms = num_sms;
+    ia.order = reinterpret_cast<int32_t *>(inpaint_order.ptr);
     e = launch_inpaint(ia, stream);
     if (e != cudaSuccess) return cuda_fail(e, "inpainting launch");
     ++launches;
@@ -777,7 +780,7 @@ dibr_status dibr_ctx::synthesize_staged(const dibr_image *img, const dibr_params
 
 void dibr_ctx::release_buffers() {
   release_band_pipeline();
-  for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth, &inpaint_scratch}) {
+  for (DevBuf *b : {&stage_in, &stage_out, &realign, &xbf_depth, &inpaint_scratch, &inpaint_order}) {
     dev_free(b->ptr);
     b->ptr = nullptr;
     b->bytes = 0;

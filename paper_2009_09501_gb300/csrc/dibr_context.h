@@ -44,7 +44,7 @@ struct dibr_ctx {
   std::mutex err_mu;
   std::string last_error, last_error_copy;
 
-  dibr::DevBuf stage_in, stage_out, realign, xbf_depth, inpaint_scratch;
+  dibr::DevBuf stage_in, stage_out, realign, xbf_depth, inpaint_scratch, inpaint_order;
   dibr::BandArgs args;  // scratch for one launch (large: keeps it off the stack)
 
   // batched launches (dibr_batch.cu)

@@ -39,28 +39,49 @@ __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
   p[2] = static_cast<uint8_t>(c >> 16);
 }
 
-__global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
-  __shared__ uint32_t cell[kStride * kStride];
+// The order in which the blocks are taken: a block with many damaged pixels takes the
+// most steps (one pass per column when its repairs creep across a wide hole), so blocks in
+// which a view has at least kHeavyDamage damaged pixels go first and the others after them;
+// a heavy block that started late would otherwise finish well after the rest.  One warp per
+// block counts its damaged pixels (lane x: block column x) and takes the next place from the
+// front or from the back of the order.
+constexpr int kHeavyDamage = 128;
+
+__global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant__ InpaintArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int blk = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (blk >= a.nblocks) return;
+  const int B = a.block, bx0 = (blk % a.nbx) * B, by0 = (blk / a.nbx) * B;
+  const int bw = min(B, a.W - bx0), bh = min(B, a.H - by0);
+  const bool col = lane < bw;
+  const uint8_t *hp = a.holes + static_cast<int64_t>(by0) * a.holes_pitch + bx0 + (col ? lane : 0);
+  uint32_t hb[kMaxBlock];
+#pragma unroll
+  for (int r = 0; r < kMaxBlock; ++r) hb[r] = col && r < bh ? hp[static_cast<int64_t>(r) * a.holes_pitch] : 0u;
+  uint32_t nl = 0, nr = 0;
+#pragma unroll
+  for (int r = 0; r < kMaxBlock; ++r) {
+    nl += hb[r] & 1u;
+    nr += (hb[r] >> 1) & 1u;
+  }
+  nl = __reduce_add_sync(0xffffffffu, nl);
+  nr = __reduce_add_sync(0xffffffffu, nr);
+  if (lane == 0) {
+    int32_t *heads = a.order + a.nblocks;
+    const bool heavy = max(nl, nr) >= static_cast<uint32_t>(kHeavyDamage);
+    const int pos = heavy ? atomicAdd(&heads[0], 1) : a.nblocks - 1 - atomicAdd(&heads[1], 1);
+    a.order[pos] = blk;
+  }
+}
+
+// One block (both views) by one warp; cell is the warp's colour frame in shared memory.
+__device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int blk, uint32_t *cell) {
   const int lane = threadIdx.x;
-  const int blk = blockIdx.x;
   const int B = a.block, W = a.W, H = a.H;
   int bx0 = 0, by0 = 0, bw = 0, bh = 0;
   if (blk < a.nblocks) {
-    // the blocks of the first and last block columns go first: the whole background moves
-    // there, so their holes are the widest (up to P/2 columns) and they take longest
-    const int nbx = a.nbx, nby = a.nblocks / a.nbx;
-    int bx, by;
-    if (nbx <= 2) {
-      bx = blk % nbx;
-      by = blk / nbx;
-    } else if (blk < 2 * nby) {
-      bx = (blk & 1) ? nbx - 1 : 0;
-      by = blk >> 1;
-    } else {
-      const int i = blk - 2 * nby;
-      bx = 1 + i % (nbx - 2);
-      by = i / (nbx - 2);
-    }
+    const int b = a.order[blk];  // heavily damaged blocks first (see inpaint_rank_kernel)
+    const int bx = b % a.nbx, by = b / a.nbx;
     bx0 = bx * B;
     by0 = by * B;
     bw = min(B, W - bx0);
@@ -304,11 +325,29 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
   }
 }
 
+// Persistent: one warp per CTA and as many CTAs as fit the GPU at once; each takes the next
+// block of the order (heaviest first) until none is left.
+__global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
+  __shared__ uint32_t cell[kStride * kStride];
+  int *next = a.order + a.nblocks + 2;
+  while (true) {
+    int i = 0;
+    if (threadIdx.x == 0) i = atomicAdd(next, 1);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= a.nblocks) break;
+    inpaint_block(a, i, cell);
+    __syncwarp();  // the cells are reused by the next block
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st) {
   if (a.nblocks <= 0) return cudaSuccess;
-  inpaint_kernel<<<a.nblocks, 32, 0, st>>>(a);
+  cudaError_t e = cudaMemsetAsync(a.order + a.nblocks, 0, 3 * sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  inpaint_rank_kernel<<<(a.nblocks + 7) / 8, 256, 0, st>>>(a);
+  inpaint_kernel<<<std::min(a.nblocks, 32 * a.sms), 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

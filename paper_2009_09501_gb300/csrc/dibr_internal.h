@@ -263,7 +263,10 @@ struct InpaintArgs {
   int64_t holes_pitch;
   uint8_t *ana, *hsbs;    // row pitch out_pitch
   int64_t out_pitch;
-  int32_t W, H, block, nbx, nblocks;
+  int32_t W, H, block, nbx, nblocks, sms;
+  int32_t *order;         // device scratch of nblocks + 3 ints: the blocks in processing order,
+                          // the two fill counters of that order and the next block to take
+                          // (zeroed before the launch)
 };
 
 // Host launchers (dibr_band.cu, dibr_xbf.cu, dibr_inpaint.cu).
