@@ -425,7 +425,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     ia.block = p->inpaint_block;
     ia.nbx = (W + ia.block - 1) / ia.block;
     ia.nblocks = ia.nbx * ((H + ia.block - 1) / ia.block);
-    if ((s = ensure(inpaint_order, sizeof(int32_t) * (static_cast<size_t>(ia.nblocks) + 3))) != DIBR_OK) return s;
+    if ((s = ensure(inpaint_order, sizeof(int32_t) * (2 * static_cast<size_t>(ia.nblocks) + 3))) != DIBR_OK) return s;
     ia.sms = num_sms;
     ia.order = reinterpret_cast<int32_t *>(inpaint_order.ptr);
     e = launch_inpaint(ia, stream);

@@ -39,12 +39,12 @@ __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
   p[2] = static_cast<uint8_t>(c >> 16);
 }
 
-// The order in which the blocks are taken: a block with many damaged pixels takes the
-// most steps (one pass per column when its repairs creep across a wide hole), so blocks in
-// which a view has at least kHeavyDamage damaged pixels go first and the others after them;
-// a heavy block that started late would otherwise finish well after the rest.  One warp per
-// block counts its damaged pixels (lane x: block column x) and takes the next place from the
-// front or from the back of the order.
+// The order in which the work items (a block in one view) are taken: an item with many
+// damaged pixels takes the most steps (one pass per column when its repairs creep across a
+// wide hole), so items with at least kHeavyDamage damaged pixels go first and the others after
+// them; a heavy item that started late would otherwise finish well after the rest.  One warp
+// per block counts the damaged pixels of both views (lane x: block column x) and places the
+// two items at the front or at the back of the order.
 constexpr int kHeavyDamage = 128;
 
 __global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant__ InpaintArgs a) {
@@ -66,22 +66,26 @@ __global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant
   }
   nl = __reduce_add_sync(0xffffffffu, nl);
   nr = __reduce_add_sync(0xffffffffu, nr);
-  if (lane == 0) {
-    int32_t *heads = a.order + a.nblocks;
-    const bool heavy = max(nl, nr) >= static_cast<uint32_t>(kHeavyDamage);
-    const int pos = heavy ? atomicAdd(&heads[0], 1) : a.nblocks - 1 - atomicAdd(&heads[1], 1);
-    a.order[pos] = blk;
+  if (lane < 2) {  // lane v places the work item of view v (2 blk + v)
+    const int items = 2 * a.nblocks;
+    int32_t *heads = a.order + items;
+    const bool heavy = (lane ? nr : nl) >= static_cast<uint32_t>(kHeavyDamage);
+    const int pos = heavy ? atomicAdd(&heads[0], 1) : items - 1 - atomicAdd(&heads[1], 1);
+    a.order[pos] = 2 * blk + lane;
   }
 }
 
-// One block (both views) by one warp; cell is the warp's colour frame in shared memory.
-__device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int blk, uint32_t *cell) {
+// One work item (a block in one view) by one warp; cell is the warp's colour frame in shared
+// memory.  The two views of a block are independent: a view's repairs change only that view
+// and its own bytes of the anaglyph (red from the left view, green and blue from the right)
+// and its half of the side-by-side frame.
+__device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int item, uint32_t *cell) {
+  const int blk = item >> 1, v = item & 1;
   const int lane = threadIdx.x;
   const int B = a.block, W = a.W, H = a.H;
   int bx0 = 0, by0 = 0, bw = 0, bh = 0;
-  if (blk < a.nblocks) {
-    const int b = a.order[blk];  // heavily damaged blocks first (see inpaint_rank_kernel)
-    const int bx = b % a.nbx, by = b / a.nbx;
+  {
+    const int bx = blk % a.nbx, by = blk / a.nbx;
     bx0 = bx * B;
     by0 = by * B;
     bw = min(B, W - bx0);
@@ -133,8 +137,7 @@ __device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int blk, uin
   auto frame_mask = [&](uint32_t fb) -> uint64_t {
     return static_cast<uint64_t>(fb & 1u) | (static_cast<uint64_t>(fb >> 1) << (bh + 1));
   };
-#pragma unroll 1
-  for (int v = 0; v < 2; ++v) {
+  do {
   uint8_t *view = a.view[v];
   const uint64_t fl = col ? (v ? fl1 : fl0) : ~0ull;  // frame rows
   // damaged block rows of this lane's column (bit y = block row y); every row beyond a
@@ -321,22 +324,22 @@ __device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int blk, uin
       }
     }
   }
-  __syncwarp();  // the frame of the next view goes into the same cells
-  }
+  } while (false);
 }
 
 // Persistent: one warp per CTA and as many CTAs as fit the GPU at once; each takes the next
-// block of the order (heaviest first) until none is left.
+// work item of the order (heaviest first) until none is left.
 __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
   __shared__ uint32_t cell[kStride * kStride];
-  int *next = a.order + a.nblocks + 2;
+  const int items = 2 * a.nblocks;
+  int *next = a.order + items + 2;
   while (true) {
     int i = 0;
     if (threadIdx.x == 0) i = atomicAdd(next, 1);
     i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= a.nblocks) break;
-    inpaint_block(a, i, cell);
-    __syncwarp();  // the cells are reused by the next block
+    if (i >= items) break;
+    inpaint_block(a, a.order[i], cell);
+    __syncwarp();  // the cells are reused by the next item
   }
 }
 
@@ -344,10 +347,10 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
 
 cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st) {
   if (a.nblocks <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(a.order + a.nblocks, 0, 3 * sizeof(int32_t), st);
+  cudaError_t e = cudaMemsetAsync(a.order + 2 * a.nblocks, 0, 3 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   inpaint_rank_kernel<<<(a.nblocks + 7) / 8, 256, 0, st>>>(a);
-  inpaint_kernel<<<std::min(a.nblocks, 32 * a.sms), 32, 0, st>>>(a);
+  inpaint_kernel<<<std::min(2 * a.nblocks, 32 * a.sms), 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -264,9 +264,9 @@ struct InpaintArgs {
   uint8_t *ana, *hsbs;    // row pitch out_pitch
   int64_t out_pitch;
   int32_t W, H, block, nbx, nblocks, sms;
-  int32_t *order;         // device scratch of nblocks + 3 ints: the blocks in processing order,
-                          // the two fill counters of that order and the next block to take
-                          // (zeroed before the launch)
+  int32_t *order;         // device scratch of 2 nblocks + 3 ints: the work items (2 block +
+                          // view) in processing order, the two fill counters of that order and
+                          // the next item to take (zeroed before the launch)
 };
 
 // Host launchers (dibr_band.cu, dibr_xbf.cu, dibr_inpaint.cu).
