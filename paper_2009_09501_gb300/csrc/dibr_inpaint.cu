@@ -1,7 +1,7 @@
 // dibr_inpaint.cu -- the iterative 2-D block inpainting of Fig. 3 (left column), run over
 // the holes of both reconstructed views after the band kernel (hole fill DIBR_FILL_INPAINT2D).
 //
-// Per block of B x B pixels and per view, one warp.  The figure's algorithm visits the
+// One warp per work item: a B x B block in one view.  The figure's algorithm visits the
 // block's damaged pixels block column by block column, in passes that repeat while some
 // pixel is repaired, and repairs a pixel once two or more of its 8 neighbours are
 // undamaged; a repair is visible at once to the visits after it.  The warp runs that order
@@ -13,12 +13,12 @@
 //
 // The damage flags of a column live in a 32-bit register of its lane (bit y = block row
 // y; the rows above and below the block never change and are kept apart); a lane reads its
-// neighbours' columns with shuffles after a step that repaired something.  Colours live in shared
-// memory with a one-pixel frame around the block.  Pixels outside the block are read as
-// the band kernel left them (they are never written by this block, and their damage
-// flags come from the holes map, which nothing changes), so blocks are independent.
-// Repaired pixels are written back into the view in place; then the anaglyph and HSBS
-// outputs are rewritten where a view changed.
+// neighbours' columns with shuffles after each step.  Colours live in shared memory with a
+// one-pixel frame around the block.  Pixels outside the block are read as the band kernel
+// left them (undamaged ones are never written; damaged ones are never read), so the items are
+// independent.  Repaired pixels are written back into the view in place, with the view's own
+// anaglyph bytes and its half of the side-by-side frame.  A rank pass orders the items
+// heavily damaged first; a persistent kernel takes them in that order.
 #include "dibr_internal.h"
 
 namespace dibr {
@@ -26,8 +26,6 @@ namespace {
 
 constexpr int kMaxBlock = 32;
 constexpr int kStride = kMaxBlock + 2;  // cells per row of a block's colour frame
-// One warp per CTA, one image block per warp; the warp takes the block's two views in turn
-// (a finished block frees its slot at once; no warp waits for another)
 
 // floor(v / (2n)) for v < 4096 and n = 2..8 as (v * ceil(65536 / 2n)) >> 16 (exact over that
 // range); index n.
