@@ -9,23 +9,25 @@
 // z-buffers and the shift tables live in registers and shared memory.
 //
 // Thread c owns the 16 columns 16c .. 16c+15 of every row.  Input rows stream into a
-// ring of shared-memory slots with 2-D TMA tensor loads (cp.async.bulk.tensor), each
-// slot's completion tracked by an mbarrier; warp 0 refills a slot right after the row
-// barrier that proves every thread is done with it.  Every wait is bounded
-// (%globaltimer); a wait that gives up sets a bit of the status word and the CTA
-// unwinds after letting its own copies land.
+// ring of shared-memory slots (one bulk copy per row, cp.async.bulk, or tensor boxes,
+// cp.async.bulk.tensor), each slot's completion tracked by an mbarrier; the middle warp
+// refills a slot right after the row barrier that proves every thread is done with it.
+// Every wait is bounded (%globaltimer); a wait that gives up sets a bit of the status word
+// and the CTA unwinds after letting its own copies land.
 //
 // Per consumer thread and row y:
 //   A  luminance of row y+2 for its 16 columns plus 2 on each side, fed into a cascade
 //      of four [1 1] row sums held in registers, which yields the vertical binomial of
 //      row y; the horizontal binomial gives D(y) for the 16 columns; clears its 16
 //      targets of this row's z-buffers (double buffered across rows).
-//   -- barrier --
 //   B  the warp scatters its 512 sources (lane-interleaved) into the left and right
-//      z-buffers with atomicMin on a ((255 - depth) << 24 | RGB) entry.
-//   -- barrier --
+//      z-buffers with atomicMin on a ((255 - depth) << 24 | RGB) entry; needs A of the
+//      row done by every warp.
 //   C  reads its 16 targets' entries, fills holes (warp scans for the nearest filled
-//      target on each side), formats and stores the outputs.
+//      target on each side), formats and stores the outputs; needs B of the row done by
+//      every warp.
+// Rows interleave as A(y+1), C(y), B(y+1): a split barrier (an mbarrier every warp arrives
+// on after A and waits on before B) and a full barrier per row.
 #include "dibr.h"
 #include "dibr_internal.h"
 #include "dibr_ptx.cuh"
