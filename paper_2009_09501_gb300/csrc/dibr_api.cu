@@ -350,7 +350,8 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   a.warp_mode = p->warp_mode;
   // The 2-D fill inpaints both views in place after the band kernel, so that kernel also
   // writes both views and the holes map: into the caller's buffers when requested, else
-  // into context scratch with the same row pitches.
+  // into context scratch with the same row pitches (two halves used by alternate frames,
+  // so that a frame's band launch may overlap the previous frame's inpainting).
   const bool inpaint = p->hole_fill == DIBR_FILL_INPAINT2D && p->warp_mode == DIBR_WARP_FORWARD;
   if (inpaint) {
     const uint32_t rgb = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HSBS;
@@ -361,8 +362,9 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     if (!(p->outputs & DIBR_OUT_LEFT)) need += static_cast<size_t>(vp) * H;
     if (!(p->outputs & DIBR_OUT_RIGHT)) need += static_cast<size_t>(vp) * H;
     if (!(p->outputs & DIBR_OUT_HOLES)) need += static_cast<size_t>(hp) * H;
-    if (need && (s = ensure(inpaint_scratch, need)) != DIBR_OK) return s;
-    size_t off = 0;
+    if (need && (s = ensure(inpaint_scratch, 2 * need)) != DIBR_OK) return s;
+    size_t off = inpaint_half * need;
+    inpaint_half ^= 1;
     auto take = [&](int slot, uint32_t bit, int64_t rows_pitch) {
       if (p->outputs & bit) return;
       a.out[slot] = inpaint_scratch.ptr + off;
@@ -392,7 +394,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
                      ? span(a.out[i], is_map_output(i) ? a.depth_pitch : a.out_pitch, H,
                             is_map_output(i) ? static_cast<int64_t>(W) : 3 * static_cast<int64_t>(W))
                      : Span{};
-  bool disjoint = may_overlap && !scratch && !inpaint;
+  bool disjoint = may_overlap && !scratch;
   for (int i = 0; i < O_COUNT; ++i) {
     if (prev_out[i].hi && meets(cur_in, prev_out[i])) disjoint = false;  // reads what it wrote
     if (!cur_out[i].hi) continue;
@@ -431,6 +433,11 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     e = launch_inpaint(ia, stream);
     if (e != cudaSuccess) return cuda_fail(e, "inpainting launch");
     ++launches;
+    // the inpainting reads and writes the band launch's outputs (views, holes map,
+    // anaglyph, side-by-side) and nothing else the next frame's band launch could touch
+    prev_band = true;
+    prev_in = Span{};
+    for (int i = 0; i < O_COUNT; ++i) prev_out[i] = cur_out[i];
   }
   return DIBR_OK;
 }

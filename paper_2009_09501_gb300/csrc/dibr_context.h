@@ -53,13 +53,15 @@ struct dibr_ctx {
   size_t batch_pinned_bytes = 0;
   cudaEvent_t batch_copy_done = nullptr;   // the last descriptor upload has read the staging
 
-  // the buffers of the last single-frame band launch, when it is the last work on a stream
-  // the context owns (the next launch may overlap it if their buffers are disjoint)
+  // the buffers of the last single-frame launch (a band launch, or the inpainting launch
+  // after one), when it is the last work on a stream the context owns: the next band launch
+  // may overlap it if their buffers are disjoint
   struct Span {
     uintptr_t lo = 0, hi = 0;
   };
   bool prev_band = false;
   Span prev_in, prev_out[dibr::O_COUNT];
+  int inpaint_half = 0;  // the half of inpaint_scratch the next 2-D fill frame uses
 
   // blocking calls with host buffers: copies and kernels of row bands overlap
   static constexpr int kMaxBands = 8;

@@ -20,6 +20,7 @@
 // anaglyph bytes and its half of the side-by-side frame.  A rank pass orders the items
 // heavily damaged first; a persistent kernel takes them in that order.
 #include "dibr_internal.h"
+#include "dibr_ptx.cuh"
 
 namespace dibr {
 namespace {
@@ -328,6 +329,11 @@ __device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int item, ui
 // Persistent: one warp per CTA and as many CTAs as fit the GPU at once; each takes the next
 // work item of the order (heaviest first) until none is left.
 __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__ InpaintArgs a) {
+  // The next band launch on the stream may start as soon as every CTA of this one runs: its
+  // CTAs take the SM slots that this launch's finished warps leave while its longest items
+  // finish (it waits for this launch before any global access unless the host knows their
+  // buffers are disjoint).
+  griddep_launch_dependents();
   __shared__ uint32_t cell[kStride * kStride];
   const int items = 2 * a.nblocks;
   int *next = a.order + items + 2;

@@ -119,6 +119,36 @@ def test_inpaint2d_4k(ctx, torch, oracle):
     assert not np.array_equal(row["left"], exp["left"])
 
 
+def test_inpaint2d_back_to_back_frames(ctx, torch, oracle):
+    # asynchronous 2-D fill frames on the context's own stream: a frame whose buffers are
+    # disjoint from the previous frame's may start its band kernel while the previous
+    # frame's inpainting runs; a frame reading the previous frame's output may not.  The
+    # views and the holes map of frames that do not request them go to context scratch.
+    H, W, P = 300, 640, 48
+    imgs = [scenes.Scene(W, H, seed=700 + k, n_objects=15).frame(0) for k in range(4)]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    kinds = [("anaglyph",), ("anaglyph", "left", "right", "holes")]
+    outs = [_alloc(torch, H, W, kinds[k % 2], True) for k in range(4)]
+    chained = _alloc(torch, H, W, ("anaglyph",), True)
+    ps = [D.make_params(max_parallax=P, depth_rule=1, outputs=kinds[k % 2], hole_fill=1, inpaint_block=32)
+          for k in range(4)]
+    torch.cuda.synchronize()
+    lib = D.load()
+    for rep in range(3):
+        for k in range(4):
+            assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(ins[k]), ps[k], D.outputs_struct(outs[k])) == 0
+        # reads the anaglyph the last frame wrote
+        assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(outs[3]["anaglyph"]), ps[0],
+                                      D.outputs_struct(chained)) == 0
+    ctx.synchronize()
+    for k in range(4):
+        exp = ref(oracle, imgs[k], kinds[k % 2], P=P, fill=1, block=32)
+        same({n: v.cpu().numpy() for n, v in outs[k].items()}, exp, "frame %d" % k)
+    exp3 = ref(oracle, imgs[3], ("anaglyph",), P=P, fill=1, block=32)["anaglyph"]
+    exp_c = ref(oracle, exp3, ("anaglyph",), P=P, fill=1, block=32)
+    same({"anaglyph": chained["anaglyph"].cpu().numpy()}, exp_c, "chained")
+
+
 def test_inpaint2d_is_refused_where_it_does_not_run(ctx, torch):
     img = torch.zeros((16, 32, 3), dtype=torch.uint8, device="cuda")
     outs = {"anaglyph": torch.zeros_like(img)}
