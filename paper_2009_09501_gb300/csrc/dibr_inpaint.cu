@@ -43,7 +43,8 @@ __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
 // wide hole), so items with at least kHeavyDamage damaged pixels go first and the others after
 // them; a heavy item that started late would otherwise finish well after the rest.  One warp
 // per block counts the damaged pixels of both views (lane x: block column x) and places the
-// two items at the front or at the back of the order.
+// two items at the front (heavy) or at the back of the order; an item without damage is not
+// placed (nothing in it changes).
 constexpr int kHeavyDamage = 128;
 
 __global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant__ InpaintArgs a) {
@@ -65,10 +66,11 @@ __global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant
   }
   nl = __reduce_add_sync(0xffffffffu, nl);
   nr = __reduce_add_sync(0xffffffffu, nr);
-  if (lane < 2) {  // lane v places the work item of view v (2 blk + v)
+  const uint32_t n = lane ? nr : nl;
+  if (lane < 2 && n > 0) {  // lane v places the work item of view v (2 blk + v), if damaged
     const int items = 2 * a.nblocks;
     int32_t *heads = a.order + items;
-    const bool heavy = (lane ? nr : nl) >= static_cast<uint32_t>(kHeavyDamage);
+    const bool heavy = n >= static_cast<uint32_t>(kHeavyDamage);
     const int pos = heavy ? atomicAdd(&heads[0], 1) : items - 1 - atomicAdd(&heads[1], 1);
     a.order[pos] = 2 * blk + lane;
   }
@@ -335,14 +337,15 @@ __global__ void __launch_bounds__(32, 32) inpaint_kernel(const __grid_constant__
   // buffers are disjoint).
   griddep_launch_dependents();
   __shared__ uint32_t cell[kStride * kStride];
-  const int items = 2 * a.nblocks;
+  // the order holds nh heavy items at its front and nl others at its back
+  const int items = 2 * a.nblocks, nh = a.order[items], nl = a.order[items + 1];
   int *next = a.order + items + 2;
   while (true) {
     int i = 0;
     if (threadIdx.x == 0) i = atomicAdd(next, 1);
     i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= items) break;
-    inpaint_block(a, a.order[i], cell);
+    if (i >= nh + nl) break;
+    inpaint_block(a, a.order[i < nh ? i : items - nl + (i - nh)], cell);
     __syncwarp();  // the cells are reused by the next item
   }
 }
