@@ -309,9 +309,18 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   // on a stream the context owns
   const bool may_overlap = owns_stream && prev_band;
   prev_band = false;
+  auto span = [](const uint8_t *ptr, int64_t row_pitch, int rows, int64_t row_bytes) {
+    Span sp;
+    sp.lo = reinterpret_cast<uintptr_t>(ptr);
+    sp.hi = sp.lo + static_cast<uintptr_t>(row_pitch) * (rows - 1) + static_cast<uintptr_t>(row_bytes);
+    return sp;
+  };
+  auto meets = [](const Span &x, const Span &y) { return x.lo < y.hi && y.lo < x.hi; };
   bool scratch = false;  // context buffers written before the band kernel
+  bool realigned = false;
   if (!tma_ok(in, pitch)) {
     scratch = true;
+    realigned = true;
     // TMA needs a 16-byte aligned base and pitch: repack into an aligned device buffer
     const int64_t ap = round_up(3 * W, 16);
     dibr_status s = ensure(realign, static_cast<size_t>(ap) * H);
@@ -330,14 +339,27 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   dibr_status s = plan_band(W, H, depth_src, in, pitch, a, smem, per_sm);
   if (s != DIBR_OK) return s;
   if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
+  Span cur_depth;  // the cross-bilateral depth this frame's band launch reads
   if (depth_src == DS_GLOBAL) {
-    scratch = true;
+    scratch = true;  // the band launch waits for the cross-bilateral one
+    // two halves used by alternate frames, so that this frame's cross-bilateral launch may
+    // start beside the previous frame's band launch: it reads this frame's input and writes
+    // a half that launch does not read, when neither meets that launch's outputs
     const int64_t dp = round_up(W, 16);
-    if ((s = ensure(xbf_depth, static_cast<size_t>(dp) * H)) != DIBR_OK) return s;
-    cudaError_t e = launch_xbf(in, pitch, W, H, p->xbf_radius, p->xbf_sigma_s, p->xbf_sigma_r,
-                               xbf_depth.ptr, dp, stream);
+    const size_t half = static_cast<size_t>(dp) * H;
+    if ((s = ensure(xbf_depth, 2 * half)) != DIBR_OK) return s;
+    uint8_t *dd = xbf_depth.ptr + xbf_half * half;
+    xbf_half ^= 1;
+    cur_depth = span(dd, dp, H, W);
+    const Span xin = span(in, pitch, H, 3 * static_cast<int64_t>(W));
+    bool after = may_overlap && !realigned && !meets(cur_depth, prev_in) && !meets(cur_depth, prev_depth);
+    for (int i = 0; i < O_COUNT; ++i)
+      if (prev_out[i].hi && (meets(xin, prev_out[i]) || meets(cur_depth, prev_out[i]))) after = false;
+    cudaError_t e = launch_xbf(in, pitch, W, H, p->xbf_radius, p->xbf_sigma_s, p->xbf_sigma_r, dd, dp, stream,
+                               after);
     if (e != cudaSuccess) return cuda_fail(e, "cross-bilateral launch");
-    a.depth_in = xbf_depth.ptr;
+    ++launches;
+    a.depth_in = dd;
     a.depth_in_pitch = dp;
   } else {
     a.depth_in = nullptr;
@@ -381,13 +403,6 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   // Overlap with the previous band launch on the stream when neither reads or writes what
   // the other writes: this launch then starts in the SMs the previous one leaves and only
   // its exit waits for it.
-  auto span = [](const uint8_t *ptr, int64_t row_pitch, int rows, int64_t row_bytes) {
-    Span sp;
-    sp.lo = reinterpret_cast<uintptr_t>(ptr);
-    sp.hi = sp.lo + static_cast<uintptr_t>(row_pitch) * (rows - 1) + static_cast<uintptr_t>(row_bytes);
-    return sp;
-  };
-  auto meets = [](const Span &x, const Span &y) { return x.lo < y.hi && y.lo < x.hi; };
   Span cur_in = span(in, pitch, H, 3 * static_cast<int64_t>(W)), cur_out[O_COUNT];
   for (int i = 0; i < O_COUNT; ++i)
     cur_out[i] = (a.outputs & kOutBits[i]) && a.out[i]
@@ -398,7 +413,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   for (int i = 0; i < O_COUNT; ++i) {
     if (prev_out[i].hi && meets(cur_in, prev_out[i])) disjoint = false;  // reads what it wrote
     if (!cur_out[i].hi) continue;
-    if (meets(cur_out[i], prev_in)) disjoint = false;  // writes what it read
+    if (meets(cur_out[i], prev_in) || meets(cur_out[i], prev_depth)) disjoint = false;  // writes what it read
     for (int j = 0; j < O_COUNT; ++j)
       if (prev_out[j].hi && meets(cur_out[i], prev_out[j])) disjoint = false;  // writes what it wrote
   }
@@ -410,6 +425,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
   if (!inpaint) {
     prev_band = true;
     prev_in = cur_in;
+    prev_depth = cur_depth;
     for (int i = 0; i < O_COUNT; ++i) prev_out[i] = cur_out[i];
   }
   if (inpaint) {
@@ -437,6 +453,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     // anaglyph, side-by-side) and nothing else the next frame's band launch could touch
     prev_band = true;
     prev_in = Span{};
+    prev_depth = Span{};
     for (int i = 0; i < O_COUNT; ++i) prev_out[i] = cur_out[i];
   }
   return DIBR_OK;

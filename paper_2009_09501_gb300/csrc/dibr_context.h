@@ -60,8 +60,9 @@ struct dibr_ctx {
     uintptr_t lo = 0, hi = 0;
   };
   bool prev_band = false;
-  Span prev_in, prev_out[dibr::O_COUNT];
+  Span prev_in, prev_depth, prev_out[dibr::O_COUNT];  // read: input, cross-bilateral depth
   int inpaint_half = 0;  // the half of inpaint_scratch the next 2-D fill frame uses
+  int xbf_half = 0;      // the half of xbf_depth the next cross-bilateral frame uses
 
   // blocking calls with host buffers: copies and kernels of row bands overlap
   static constexpr int kMaxBands = 8;

@@ -275,8 +275,10 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
 // launch is a batch launch of the same call).
 cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st);
 cudaError_t launch_inpaint(const InpaintArgs &a, cudaStream_t st);
+// after: may start beside the previous launch on the stream (its buffers are disjoint from
+// this launch's), completing only after it.
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius,
                        float sigma_s, float sigma_r, uint8_t *D, int64_t dpitch,
-                       cudaStream_t st);
+                       cudaStream_t st, bool after = false);
 
 }  // namespace dibr

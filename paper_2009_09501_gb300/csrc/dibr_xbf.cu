@@ -17,6 +17,7 @@
 // the special-function unit's low rate, is an exact mantissa trick, so the exp2 is the
 // only such operation per tap.
 #include "dibr_internal.h"
+#include "dibr_ptx.cuh"
 
 namespace dibr {
 namespace {
@@ -52,7 +53,8 @@ __device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float yq, floa
 
 template <int R>
 __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
-                                                       float as, float ar, uint8_t *__restrict__ D, int64_t dpitch) {
+                                                       float as, float ar, uint8_t *__restrict__ D, int64_t dpitch,
+                                                       int after) {
   __shared__ uint2 px[kTY + 2 * R][kTX + 2 * R];  // colour 0x00BBGGRR, luminance as float bits
   const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY;
   constexpr int ax = kTX + 2 * R, ay = kTY + 2 * R;
@@ -72,7 +74,10 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
   __syncthreads();
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   const int x = bx + tx, y = by + ty;
-  if (x >= W || y >= H) return;
+  if (x >= W || y >= H) {
+    if (after) griddep_wait();
+    return;
+  }
   const uint2 pc = px[ty + R][tx + R];
   const uint32_t cp = pc.x;
   const float yp = __uint_as_float(pc.y);
@@ -99,31 +104,42 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
   const float q = floorf(num / den + 0.5f);
   const int v = static_cast<int>(yp) + static_cast<int>(q);
   D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
+  // launched to run beside the previous launch on the stream (whose buffers the host found
+  // disjoint from this one's): complete only after it, so that the stream order holds
+  if (after) griddep_wait();
 }
 
 template <int R>
 cudaError_t launch_r(const uint8_t *rgb, int64_t pitch, int W, int H, float as, float ar, uint8_t *D, int64_t dpitch,
-                     cudaStream_t st) {
-  dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
-  xbf_kernel<R><<<grid, kTX * kTY, 0, st>>>(rgb, pitch, W, H, as, ar, D, dpitch);
-  return cudaGetLastError();
+                     cudaStream_t st, bool after) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+  cfg.blockDim = dim3(kTX * kTY);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = after ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, xbf_kernel<R>, rgb, pitch, W, H, as, ar, D, dpitch, after ? 1 : 0);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_xbf(const uint8_t *rgb, int64_t pitch, int W, int H, int radius, float sigma_s,
-                       float sigma_r, uint8_t *D, int64_t dpitch, cudaStream_t st) {
+                       float sigma_r, uint8_t *D, int64_t dpitch, cudaStream_t st, bool after) {
   const float as = static_cast<float>(1.0 / (2.0 * static_cast<double>(sigma_s) * sigma_s));
   const float ar = static_cast<float>(1.0 / (2.0 * static_cast<double>(sigma_r) * sigma_r));
   switch (radius) {
-    case 1: return launch_r<1>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 2: return launch_r<2>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 3: return launch_r<3>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 4: return launch_r<4>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 5: return launch_r<5>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 6: return launch_r<6>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 7: return launch_r<7>(rgb, pitch, W, H, as, ar, D, dpitch, st);
-    case 8: return launch_r<8>(rgb, pitch, W, H, as, ar, D, dpitch, st);
+    case 1: return launch_r<1>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 2: return launch_r<2>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 3: return launch_r<3>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 4: return launch_r<4>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 5: return launch_r<5>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 6: return launch_r<6>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 7: return launch_r<7>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
+    case 8: return launch_r<8>(rgb, pitch, W, H, as, ar, D, dpitch, st, after);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -272,6 +272,46 @@ def test_host_buffers_band_counts(ctx, torch, oracle, bands):
         assert_same(outs, ref, "%d bands %dx%d" % (bands, W, H))
 
 
+def test_xbf_back_to_back_frames(ctx, torch):
+    # cross-bilateral frames on the context's own stream: a frame's cross-bilateral launch
+    # may start beside the previous frame's band launch when their buffers are disjoint (the
+    # depth scratch alternates between two halves); a frame reading the previous frame's
+    # output may not.  Each frame must equal the same frame computed alone (the kernels are
+    # deterministic).
+    H, W, P = 360, 640, 32
+    imgs = [scenes.Scene(W, H, seed=800 + k, n_objects=15).frame(0) for k in range(4)]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    want = ("anaglyph", "left", "depth")
+    p = gpu_params(want, max_parallax=P, depth_rule=2)
+    pc = gpu_params(("anaglyph",), max_parallax=P, depth_rule=2)
+
+    def alloc(names):
+        return {n: torch.zeros((H, W) if n in D.MAP_OUTPUTS else (H, W, 3), dtype=torch.uint8, device="cuda")
+                for n in names}
+
+    alone = []
+    for k in range(4):
+        o = alloc(want)
+        ctx.synthesize_image(ins[k], p, o)
+        alone.append({n: v.cpu().numpy() for n, v in o.items()})
+    outs = [alloc(want) for _ in range(4)]
+    chained = alloc(("anaglyph",))
+    torch.cuda.synchronize()
+    lib = D.load()
+    for rep in range(3):
+        for k in range(4):
+            assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(ins[k]), p, D.outputs_struct(outs[k])) == 0
+        # reads the left view frame 3 just wrote
+        assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(outs[3]["left"]), pc, D.outputs_struct(chained)) == 0
+    ctx.synchronize()
+    for k in range(4):
+        assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, alone[k], "frame %d" % k)
+    c_alone = alloc(("anaglyph",))
+    ctx.synthesize_image(outs[3]["left"], pc, c_alone)
+    assert_same({"anaglyph": chained["anaglyph"].cpu().numpy()}, {"anaglyph": c_alone["anaglyph"].cpu().numpy()},
+                "chained frame")
+
+
 def test_back_to_back_frames_overlap_only_when_independent(ctx, torch, oracle):
     # consecutive asynchronous frames on the context's own stream: disjoint buffers may
     # overlap on the GPU, a frame reading the previous frame's output must not
