@@ -16,7 +16,7 @@ Prints one JSON line (rank 0):
   cpu_baseline  the CPU oracle on this host's cores (band-parallel over row bands), on a
              bounded sample of frames;
   clocks     SM clock samples taken by nvidia-smi during the timed region.
---impl reference times the CPU oracle alone on the same workload (see DESIGN.md).
+--impl reference times the CPU oracle alone on the same workload.
 """
 import argparse
 import json
