@@ -45,7 +45,7 @@ __device__ __forceinline__ void store_rgb(uint8_t *p, uint32_t c) {
 // per block counts the damaged pixels of both views (lane x: block column x) and places the
 // two items at the front (heavy) or at the back of the order; an item without damage is not
 // placed (nothing in it changes).
-constexpr int kHeavyDamage = 128;
+constexpr int kHeavyDamage = 256;
 
 __global__ void __launch_bounds__(256) inpaint_rank_kernel(const __grid_constant__ InpaintArgs a) {
   const int lane = threadIdx.x & 31;
