@@ -260,12 +260,12 @@ __device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int item, ui
       const int b = t - x2;
       return b < 0 ? 0u : b >= 31 ? 0xFFFFFFFFu : (2u << b) - 1u;
     };
-    // the first step at or after t with a visit to make, over the warp (INT_MAX: none)
+    // the first step at or after t with a visit to make, over the warp (INT_MAX: none): t
+    // when the lane has a dirty row it has reached (visited within 4 steps), else the first
+    // visit of its lowest dirty row, 2x + y; both are max(t, 2x + lowest dirty row)
     auto next_step = [&](int t) -> int {
       const uint32_t dd = col ? own & dirty : 0u;
-      int n = 0x7FFFFFFF;
-      if (dd & reached(t)) n = t;                  // visited within 4 steps
-      else if (dd) n = x2 + __ffs(dd) - 1;         // its first visit
+      const int n = dd ? max(t, x2 + __ffs(dd) - 1) : 0x7FFFFFFF;
       return __reduce_min_sync(0xffffffffu, n);
     };
     for (int t = next_step(0); t != 0x7FFFFFFF; t = next_step(t + 1)) {
