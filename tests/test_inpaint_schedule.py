@@ -36,12 +36,14 @@ def _model_block(view, dmg, bx0, by0, bw, bh):
 
     t = 0
     while True:
-        # the next step at which some column has a dirty damaged pixel to visit
+        # the next step at which some column has a dirty damaged pixel to visit: per column,
+        # max(t, 2x + its lowest dirty row) (t when it has reached one, else that row's first
+        # visit)
         nxt = None
         for x in range(bw):
             rows = [j - 1 for j in range(1, bh + 1) if flag[x + 1, j] and (x + 1, j) in dirty]
             if rows:
-                n = t if any(y <= t - 2 * x for y in rows) else 2 * x + min(rows)
+                n = max(t, 2 * x + min(rows))
                 nxt = n if nxt is None else min(nxt, n)
         if nxt is None:
             break
