@@ -331,6 +331,45 @@ def test_xbf_back_to_back_frames(ctx, torch):
                 "chained frame")
 
 
+def test_mixed_mode_frames_back_to_back(ctx, torch):
+    # row-fill, 2-D fill and cross-bilateral frames interleaved on the context's own stream:
+    # each launch may start beside the previous frame's last one only when their buffers are
+    # disjoint, whatever mode either frame had; every frame must equal the same frame computed
+    # alone (the kernels are deterministic), also one that reads the previous frame's output
+    H, W, P = 200, 480, 24
+    imgs = [scenes.Scene(W, H, seed=950 + k, n_objects=12).frame(0) for k in range(6)]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    want = ("anaglyph", "left")
+    modes = [dict(), dict(hole_fill=1), dict(depth_rule=2), dict(hole_fill=1), dict(), dict(depth_rule=2)]
+    ps = [D.make_params(max_parallax=P, depth_rule=m.get("depth_rule", 1), outputs=want,
+                        hole_fill=m.get("hole_fill", 0), inpaint_block=16) for m in modes]
+
+    def alloc():
+        return {n: torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda") for n in want}
+
+    alone = []
+    for k in range(6):
+        o = alloc()
+        ctx.synthesize_image(ins[k], ps[k], o)
+        alone.append({n: v.cpu().numpy() for n, v in o.items()})
+    outs = [alloc() for _ in range(6)]
+    chained = alloc()
+    torch.cuda.synchronize()
+    lib = D.load()
+    for rep in range(3):
+        for k in range(6):
+            assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(ins[k]), ps[k], D.outputs_struct(outs[k])) == 0
+        # a cross-bilateral frame reading the left view the last frame wrote
+        assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(outs[5]["left"]), ps[2], D.outputs_struct(chained)) == 0
+    ctx.synchronize()
+    for k in range(6):
+        assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, alone[k], "frame %d (%s)" % (k, modes[k]))
+    c_alone = alloc()
+    ctx.synthesize_image(outs[5]["left"], ps[2], c_alone)
+    assert_same({n: v.cpu().numpy() for n, v in chained.items()}, {n: v.cpu().numpy() for n, v in c_alone.items()},
+                "chained frame")
+
+
 def test_back_to_back_frames_overlap_only_when_independent(ctx, torch, oracle):
     # consecutive asynchronous frames on the context's own stream: disjoint buffers may
     # overlap on the GPU, a frame reading the previous frame's output must not
