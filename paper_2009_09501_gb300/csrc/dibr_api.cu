@@ -186,12 +186,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
-dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, BandArgs &a,
-                               int &smem, int &per_sm) {
+dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, int zguard,
+                               BandArgs &a, int &smem, int &per_sm) {
   a.W = W;
   a.H = H;
   a.nch = (W + kChunk - 1) / kChunk;
   a.nc = round_up(a.nch, 32);  // one 16-pixel chunk per consumer thread
+  a.zguard = zguard;
   // how rows reach shared memory: the tuned mode when the image allows it, else the
   // automatic choice (one bulk copy per row when rows are whole 16-byte units)
   const bool aligned = (reinterpret_cast<uintptr_t>(in) & 15u) == 0 && (pitch & 15) == 0;
@@ -236,7 +237,7 @@ dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, 
   // at most 128 registers per thread (the kernel's launch bound) and 2048 threads per SM
   const int max_per = std::max(1, std::min(65536 / (a.nc * 128), 2048 / a.nc));
   auto per_for = [&](int nb) {
-    const int tot = band_smem_layout(nb, a.srow, a.nch, depth_src).total;
+    const int tot = band_smem_layout(nb, a.srow, a.nch, a.nc / 32, zguard).total;
     if (tot > max_smem) return 0;
     int per = std::min(max_per, smem_per_sm / (tot + 1024));
     if (tuning.ctas_per_sm > 0) per = std::min(per, tuning.ctas_per_sm);
@@ -252,7 +253,7 @@ dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, 
   for (int k = min_nb; k <= max_nb; ++k)
     if (per_for(k) == best) nb = k;
   a.nb = nb;
-  smem = band_smem_layout(nb, a.srow, a.nch, depth_src).total;
+  smem = band_smem_layout(nb, a.srow, a.nch, a.nc / 32, zguard).total;
   per_sm = best;
   a.grid = std::max(1, std::min(H, num_sms * per_sm));
   a.row0 = 0;
@@ -296,6 +297,15 @@ dibr_status dibr_ctx::encode_input(BandArgs &a, const uint8_t *dev_rgb, int64_t 
   return DIBR_OK;
 }
 
+// Every requested RGB output and the output pitch are 16-byte aligned: whole 16-column
+// chunks are stored as three 16-byte words.
+static int aligned_rgb_outputs(const BandArgs &a) {
+  uintptr_t bits = static_cast<uintptr_t>(a.out_pitch);
+  for (int i = 0; i < O_COUNT; ++i)
+    if (!is_map_output(i) && (a.outputs & kOutBits[i])) bits |= reinterpret_cast<uintptr_t>(a.out[i]);
+  return (bits & 15u) == 0 ? 1 : 0;
+}
+
 static bool tma_ok(const uint8_t *p, int64_t pitch) {
   return (reinterpret_cast<uintptr_t>(p) & 15u) == 0 && (pitch & 15) == 0;
 }
@@ -336,7 +346,8 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
                                                          : DS_GLOBAL;
   BandArgs &a = args;
   int smem = 0, per_sm = 1;
-  dibr_status s = plan_band(W, H, depth_src, in, pitch, a, smem, per_sm);
+  shift_tables(p, a.lut_h, a.lut_n);
+  dibr_status s = plan_band(W, H, depth_src, in, pitch, zguard_of(a.lut_h), a, smem, per_sm);
   if (s != DIBR_OK) return s;
   if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
   Span cur_depth;  // the cross-bilateral depth this frame's band launch reads
@@ -399,7 +410,7 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
     a.depth_pitch = hp;
     a.outputs |= DIBR_OUT_LEFT | DIBR_OUT_RIGHT | DIBR_OUT_HOLES;
   }
-  shift_tables(p, a.lut_h, a.lut_n);
+  a.fast_store = aligned_rgb_outputs(a);
   // Overlap with the previous band launch on the stream when neither reads or writes what
   // the other writes: this launch then starts in the SMs the previous one leaves and only
   // its exit waits for it.
@@ -675,7 +686,8 @@ dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params
   BandArgs &a = args;
   int smem = 0, per_sm = 1;
   const int depth_src = p->depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
-  if ((s = plan_band(W, H, depth_src, stage_in.ptr, ap, a, smem, per_sm)) != DIBR_OK) return s;
+  shift_tables(p, a.lut_h, a.lut_n);
+  if ((s = plan_band(W, H, depth_src, stage_in.ptr, ap, zguard_of(a.lut_h), a, smem, per_sm)) != DIBR_OK) return s;
   if ((s = encode_input(a, stage_in.ptr, ap)) != DIBR_OK) return s;
   a.depth_in = nullptr;
   a.depth_in_pitch = 0;
@@ -684,7 +696,7 @@ dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params
   a.depth_pitch = dp;
   a.outputs = p->outputs;
   a.warp_mode = p->warp_mode;
-  shift_tables(p, a.lut_h, a.lut_n);
+  a.fast_store = aligned_rgb_outputs(a);
   const int slots = a.grid;  // CTAs of a whole-frame launch
   auto band_row = [&](int k) { return static_cast<int>(static_cast<int64_t>(k) * H / bands); };
   // the copy streams start after the work already queued on the context's stream

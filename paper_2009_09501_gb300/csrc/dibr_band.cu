@@ -11,23 +11,28 @@
 // Thread c owns the 16 columns 16c .. 16c+15 of every row.  Input rows stream into a
 // ring of shared-memory slots (one bulk copy per row, cp.async.bulk, or tensor boxes,
 // cp.async.bulk.tensor), each slot's completion tracked by an mbarrier; the middle warp
-// refills a slot right after the row barrier that proves every thread is done with it.
-// Every wait is bounded (%globaltimer); a wait that gives up sets a bit of the status word
-// and the CTA unwinds after letting its own copies land.
+// refills a slot once every warp has scattered the row it held.
 //
 // Per consumer thread and row y:
 //   A  luminance of row y+2 for its 16 columns plus 2 on each side, fed into a cascade
 //      of four [1 1] row sums held in registers, which yields the vertical binomial of
-//      row y; the horizontal binomial gives D(y) for the 16 columns; clears its 16
-//      targets of this row's z-buffers (double buffered across rows).
+//      row y; the horizontal binomial gives D(y) for the 16 columns, stored as 255 - D.
 //   B  the warp scatters its 512 sources (lane-interleaved) into the left and right
-//      z-buffers with atomicMin on a ((255 - depth) << 24 | RGB) entry; needs A of the
-//      row done by every warp.
-//   C  reads its 16 targets' entries, fills holes (warp scans for the nearest filled
-//      target on each side), formats and stores the outputs; needs B of the row done by
-//      every warp.
-// Rows interleave as A(y+1), C(y), B(y+1): a split barrier (an mbarrier every warp arrives
-// on after A and waits on before B) and a full barrier per row.
+//      z-buffers with a shared-memory atomic minimum of ((255 - D) << 24 | RGB).  The
+//      z-buffer rows carry guard targets on both sides, as wide as the largest shift,
+//      so a source whose target falls outside the row lands in a guard: no bounds test.
+//   C  reads its 16 targets' entries, fills holes (register sweeps; the entries carried
+//      across chunks come from the neighbouring lanes by shuffle, across warps from a
+//      per-warp summary in shared memory), formats and stores the outputs, and clears
+//      its warp's targets for the row two rows later.
+// Rows interleave as A(y+1), C(y), B(y+1).  There is no CTA-wide barrier per row: C of a
+// row waits on an mbarrier every warp arrives on after B of that row, and a warp that
+// needs an entry from outside its own targets waits on a second one every warp arrives
+// on once it has published its summary and cleared its targets.  Every wait is bounded
+// (%globaltimer); a wait that gives up sets a bit of the status word and the CTA unwinds
+// after letting its own copies land.
+#include <atomic>
+
 #include "dibr.h"
 #include "dibr_internal.h"
 #include "dibr_ptx.cuh"
@@ -35,7 +40,17 @@
 namespace dibr {
 namespace {
 
-constexpr int kNoTarget = 0x7FFFFFFF;
+constexpr uint32_t kAll = 0xFFFFFFFFu;
+
+// z-buffer entry: ((255 - depth) << 24) | RGB of the source, reduced with an atomic
+// minimum into a buffer initialised to kEmpty.  The smallest entry has the largest depth
+// (nearest source).  Two sources with equal depth have equal shifts and so never meet on
+// one target, so the colour bits never decide a collision; the winner's colour is read
+// straight from its entry.  kEmpty cannot be a real entry: it would need depth 0 for a
+// white pixel, and every depth rule gives a white pixel a depth of at least 1 (binomial:
+// its own weight 36/256; luminance: 255; cross-bilateral: its own weight 1 among at most
+// 289).
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 __device__ __forceinline__ uint32_t bsel(const uint32_t *w, int j) {
   return (w[j >> 2] >> (8 * (j & 3))) & 0xFFu;
@@ -48,18 +63,18 @@ __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b) {
   return __umulhi(299u * r + 587u * g + 114u * b + 500u, 4294968u);
 }
 
-// The same luminance of the pixel held in bytes 0..2 (S = 0) or 1..3 (S = 8) of w, as
-// three byte dot products: 299 = 255 + 44, 587 = 255 + 255 + 77, 114.
-template <int S>
-__device__ __forceinline__ uint32_t luma_dp(uint32_t w) {
-  uint32_t n = __dp4a(w, 0x0072FFFFu << S, 500u);
-  n = __dp4a(w, 0x0000FF2Cu << S, n);
-  n = __dp4a(w, 0x00004D00u << S, n);
-  return __umulhi(n, 4294968u);
+// The same luminance of a pixel word holding R, G, B, G in bytes 0..3: two byte dot
+// products, 255 R + 510 G + 114 B and 44 R + 77 G (299 = 255 + 44, 587 = 2 * 255 + 77).
+__device__ __forceinline__ uint32_t luma_rgbg(uint32_t w) {
+  const uint32_t n = __dp4a(w, 0xFF72FFFFu, 500u);
+  return __umulhi(__dp4a(w, 0x00004D2Cu, n), 4294968u);
 }
 
-// Luminance of one packed pixel word (R, G, B in the low three bytes).
-__device__ __forceinline__ uint32_t luma_px(uint32_t c) { return luma_dp<0>(c); }
+// Pixel word (R, G, B, G) of the colour at byte offset r (0..3) of the byte pair lo, hi.
+template <int R>
+__device__ __forceinline__ uint32_t rgbg_at(uint32_t lo, uint32_t hi) {
+  return __byte_perm(lo, hi, R | ((R + 1) << 4) | ((R + 2) << 8) | ((R + 1) << 12));
+}
 
 // Luminance of columns x0-2 .. x0+17 (clamped to [0, W-1]) of one input row held in
 // shared memory, as 10 words of two 16-bit lanes: yp[2q] = columns (4q, 4q+2) and
@@ -67,10 +82,9 @@ __device__ __forceinline__ uint32_t luma_px(uint32_t c) { return luma_dp<0>(c); 
 __device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32_t (&yp)[10]) {
   // bytes 3*x0-8 .. 3*x0+55 (8-byte and 16-byte aligned loads); column j of the window at
   // byte 2+3j.  At the row's ends the loads reach past it into neighbouring shared memory
-  // (the ring's other slots, the table before it, the depth row after it); those columns
-  // are replaced below by the row's first or last column.
-  uint32_t y[20];
-  uint32_t b[16];
+  // (another ring slot, the summaries before the ring, the depth row after it); those
+  // columns are replaced below by the row's first or last column.
+  uint32_t b[17];
   const uint2 l = *reinterpret_cast<const uint2 *>(row + 3 * x0 - 8);
   const uint4 m0 = *reinterpret_cast<const uint4 *>(row + 3 * x0);
   const uint4 m1 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 16);
@@ -80,39 +94,75 @@ __device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32
   b[2] = m0.x; b[3] = m0.y; b[4] = m0.z; b[5] = m0.w;
   b[6] = m1.x; b[7] = m1.y; b[8] = m1.z; b[9] = m1.w;
   b[10] = m2.x; b[11] = m2.y; b[12] = m2.z; b[13] = m2.w;
-  b[14] = r.x; b[15] = r.y;
+  b[14] = r.x; b[15] = r.y; b[16] = r.y;
+  uint32_t y[20];
 #pragma unroll
   for (int j = 0; j < 20; ++j) {
     const int o = 2 + 3 * j, q = o >> 2;
-    if ((o & 3) == 0) y[j] = luma_dp<0>(b[q]);
-    else if ((o & 3) == 1) y[j] = luma_dp<8>(b[q]);
-    else y[j] = luma_dp<0>(__funnelshift_r(b[q], b[q + 1], 8 * (o & 3)));
+    uint32_t w;
+    switch (o & 3) {
+      case 0: w = rgbg_at<0>(b[q], b[q + 1]); break;
+      case 1: w = rgbg_at<1>(b[q], b[q + 1]); break;
+      case 2: w = rgbg_at<2>(b[q], b[q + 1]); break;
+      default: w = rgbg_at<3>(b[q], b[q + 1]); break;
+    }
+    y[j] = luma_rgbg(w);
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    yp[2 * q] = y[4 * q] | (y[4 * q + 2] << 16);
-    yp[2 * q + 1] = y[4 * q + 1] | (y[4 * q + 3] << 16);
+    yp[2 * q] = __byte_perm(y[4 * q], y[4 * q + 2], 0x5410);
+    yp[2 * q + 1] = __byte_perm(y[4 * q + 1], y[4 * q + 3], 0x5410);
   }
   // clamp to the row: the columns before 0 and after W-1 take column 0 and column W-1
   // (window column j sits in word 2 * (j / 4) + j % 2, high lane when j / 2 is odd)
-  if (x0 == 0) {  // window columns 0 and 1 (low lanes of words 0 and 1) <- window column 2
-    const uint32_t yf = yp[0] >> 16;
-    yp[0] = (yp[0] & 0xFFFF0000u) | yf;
-    yp[1] = (yp[1] & 0xFFFF0000u) | yf;
-  }
-  if (x0 + 16 == W) {  // window columns 18 and 19 (high lanes of words 8, 9) <- column 17
-    const uint32_t yl = yp[9] << 16;
-    yp[8] = (yp[8] & 0xFFFFu) | yl;
-    yp[9] = (yp[9] & 0xFFFFu) | yl;
-  } else if (x0 + 18 > W) {
-    const uint8_t *pl = row + 3 * (W - 1);
-    const uint32_t ylast = luma8(pl[0], pl[1], pl[2]);
+  if (x0 == 0 || x0 + 18 > W) {
+    if (x0 == 0) {  // window columns 0 and 1 (low lanes of words 0 and 1) <- window column 2
+      const uint32_t yf = yp[0] >> 16;
+      yp[0] = (yp[0] & 0xFFFF0000u) | yf;
+      yp[1] = (yp[1] & 0xFFFF0000u) | yf;
+    }
+    if (x0 + 16 == W) {  // window columns 18 and 19 (high lanes of words 8, 9) <- column 17
+      const uint32_t yl = yp[9] << 16;
+      yp[8] = (yp[8] & 0xFFFFu) | yl;
+      yp[9] = (yp[9] & 0xFFFFu) | yl;
+    } else if (x0 + 18 > W) {
+      const uint8_t *pl = row + 3 * (W - 1);
+      const uint32_t ylast = luma8(pl[0], pl[1], pl[2]);
 #pragma unroll
-    for (int j = 3; j < 20; ++j) {
-      const int w = 2 * (j >> 2) + (j & 1), sh = 16 * ((j >> 1) & 1);
-      if (x0 - 2 + j > W - 1) yp[w] = (yp[w] & ~(0xFFFFu << sh)) | (ylast << sh);
+      for (int j = 3; j < 20; ++j) {
+        const int w = 2 * (j >> 2) + (j & 1), sh = 16 * ((j >> 1) & 1);
+        if (x0 - 2 + j > W - 1) yp[w] = (yp[w] & ~(0xFFFFu << sh)) | (ylast << sh);
+      }
     }
   }
+}
+
+// Luminance of the 16 columns x0 .. x0+15 of a row in shared memory, packed 4 per word
+// (columns past the row's end take whatever their bytes give: they are never used).
+__device__ __forceinline__ uint4 luma16(const uint8_t *row, int x0) {
+  const uint4 m0 = *reinterpret_cast<const uint4 *>(row + 3 * x0);
+  const uint4 m1 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 16);
+  const uint4 m2 = *reinterpret_cast<const uint4 *>(row + 3 * x0 + 32);
+  const uint32_t b[13] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w, m2.x, m2.y, m2.z, m2.w, m2.w};
+  uint32_t y[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int o = 3 * j, q = o >> 2;
+    uint32_t w;
+    switch (o & 3) {
+      case 0: w = rgbg_at<0>(b[q], b[q + 1]); break;
+      case 1: w = rgbg_at<1>(b[q], b[q + 1]); break;
+      case 2: w = rgbg_at<2>(b[q], b[q + 1]); break;
+      default: w = rgbg_at<3>(b[q], b[q + 1]); break;
+    }
+    y[j] = luma_rgbg(w);
+  }
+  uint32_t d[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    d[k] = __byte_perm(__byte_perm(y[4 * k], y[4 * k + 1], 0x0040), __byte_perm(y[4 * k + 2], y[4 * k + 3], 0x0040),
+                       0x5410);
+  return make_uint4(d[0], d[1], d[2], d[3]);
 }
 
 // Vertical binomial [1 4 6 4 1] as four cascaded [1 1] sums over the stream of
@@ -159,7 +209,8 @@ struct VCascade {
 };
 
 // Horizontal binomial of the vertical sums and rounding: D = (sum + 128) >> 8 for the 16
-// own columns (window columns 2..17), packed 4 per word.
+// own columns (window columns 2..17), packed 4 per word.  Both lanes of a sum word stay
+// below 65536 after the rounding offset, so byte 1 of each lane is its rounded result.
 __device__ __forceinline__ uint4 binom_h(const uint32_t (&V)[10]) {
   uint32_t d[4];
 #pragma unroll
@@ -167,42 +218,18 @@ __device__ __forceinline__ uint4 binom_h(const uint32_t (&V)[10]) {
     const uint32_t E0 = V[2 * k], O0 = V[2 * k + 1], E1 = V[2 * k + 2], O1 = V[2 * k + 3];
     const uint32_t se = __byte_perm(E0, E1, 0x5432);  // (V[4k+2], V[4k+4])
     const uint32_t so = __byte_perm(O0, O1, 0x5432);  // (V[4k+3], V[4k+5])
-    const uint32_t pe = E0 + E1 + 4u * (O0 + so) + 6u * se;  // columns 4k, 4k+2
-    const uint32_t po = O0 + O1 + 4u * (se + E1) + 6u * so;  // columns 4k+1, 4k+3
-    const uint32_t de = ((pe + 0x00800080u) >> 8) & 0x00FF00FFu;
-    const uint32_t dd = ((po + 0x00800080u) >> 8) & 0x00FF00FFu;
-    d[k] = de | (dd << 8);
+    const uint32_t pe = E0 + E1 + 0x00800080u + 4u * (O0 + so) + 6u * se;  // columns 4k, 4k+2
+    const uint32_t po = O0 + O1 + 0x00800080u + 4u * (se + E1) + 6u * so;  // columns 4k+1, 4k+3
+    d[k] = __byte_perm(pe, po, 0x7351);
   }
   return make_uint4(d[0], d[1], d[2], d[3]);
 }
-
-// Target offsets of a source from its packed table entry: -hL (low half) and -hR (high
-// half), both sign-extended.
-__device__ __forceinline__ int shift_l(uint32_t w) { return static_cast<int>(w << 16) >> 16; }
-__device__ __forceinline__ int shift_r(uint32_t w) { return static_cast<int>(w) >> 16; }
-
-// z-buffer entry: ((255 - depth) << 24) | RGB of the source, reduced with atomicMin
-// into a buffer initialised to kEmpty.  The smallest entry has the largest depth
-// (nearest source).  Two sources with equal depth have equal shifts and so never meet
-// on one target, so the colour bits never decide a collision; the winner's colour is
-// read straight from its entry.  kEmpty cannot be a real entry: it would need depth 0
-// for a white pixel, and every depth rule gives a white pixel a depth of at least 1
-// (binomial: its own weight 36/256; luminance: 255; cross-bilateral: its own weight 1
-// among at most 289).
-constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // Packed RGB (3 bytes) of column x of a row in global memory (byte loads: nothing past the
 // pixel is read).
 __device__ __forceinline__ uint32_t rgb_at_global(const uint8_t *row, int x) {
   const uint8_t *p = row + 3 * static_cast<int64_t>(x);
   return static_cast<uint32_t>(p[0]) | (static_cast<uint32_t>(p[1]) << 8) | (static_cast<uint32_t>(p[2]) << 16);
-}
-
-// Packed RGB (3 bytes) of column x of a row held in shared memory.
-__device__ __forceinline__ uint32_t rgb_at(const uint8_t *row, int x) {
-  const uint32_t off = 3u * static_cast<uint32_t>(x);
-  const uint32_t *wp = reinterpret_cast<const uint32_t *>(row + (off & ~3u));
-  return __funnelshift_r(wp[0], wp[1], (off & 3u) * 8u) & 0xFFFFFFu;
 }
 
 // Sixteen 3-byte colours (low bytes of c[i]) packed into 12 words.
@@ -213,119 +240,6 @@ __device__ __forceinline__ void pack16(const uint32_t (&c)[16], uint32_t (&w)[12
     w[3 * k + 1] = __byte_perm(c[4 * k + 1], c[4 * k + 2], 0x5421);
     w[3 * k + 2] = __byte_perm(c[4 * k + 2], c[4 * k + 3], 0x6542);
   }
-}
-
-// Nearest filled target at or below t (or -1) / at or above t (or kNoTarget), searched
-// by the whole warp 32 targets at a time (all lanes call it together): the path for
-// holes whose neighbours lie outside the warp's own targets.
-__device__ __noinline__ int warp_walk_left(const uint32_t *zb, int t, int lane) {
-  for (int base = t; base >= 0; base -= 32) {
-    const int i = base - lane;
-    const uint32_t b = __ballot_sync(0xffffffffu, i >= 0 && zb[i] != kEmpty);
-    if (b) return base - (__ffs(b) - 1);
-  }
-  return -1;
-}
-
-__device__ __noinline__ int warp_walk_right(const uint32_t *zb, int t, int W, int lane) {
-  for (int base = t; base < W; base += 32) {
-    const int i = base + lane;
-    const uint32_t b = __ballot_sync(0xffffffffu, i < W && zb[i] != kEmpty);
-    if (b) return base + (__ffs(b) - 1);
-  }
-  return kNoTarget;
-}
-
-// Entries shown by the 16 targets of this thread in one view: the z-buffer winner, or
-// for a hole the winner of the nearest filled target on its farther side -- of the
-// nearest filled targets to its left and right, the one whose winner has the smaller
-// depth (the left one on a tie, the only one at a row edge); the input pixel at the hole
-// when the row has no filled target.
-//
-// Two register sweeps: left to right carrying the last filled key into the holes, then
-// right to left carrying the last filled key and keeping it where it is strictly
-// farther.  Entries are (255 - depth) << 24 | colour, so "c strictly farther than k" is
-// the unsigned compare c > (k | 0xFFFFFF).  The keys carried into the chunk come from
-// the nearest lane on each side with a filled target (ballot + shuffle) or, past the
-// warp's 512 targets, from a warp-wide search of the z-buffer.  A missing right key
-// carries in as 0, which is never strictly farther; holes with no left key (row starts)
-// are set afterwards on a path of their own.
-// Returns the thread's hole bits (bit j: no source reached target x0 + j).
-__device__ __forceinline__ uint32_t resolve_view(const uint32_t *zb, const uint8_t *grow, int x0, int npx, int W,
-                                                 int lane, int warp_lo, int warp_hi, uint32_t (&k)[16]) {
-  const uint32_t zs = smem_addr(zb);
-  if (npx > 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 u = lds_u32x4(zs + 4u * (x0 + 4 * q));
-      k[4 * q] = u.x; k[4 * q + 1] = u.y; k[4 * q + 2] = u.z; k[4 * q + 3] = u.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) k[i] = 0u;
-  }
-  const uint32_t rowmask = npx >= 16 ? 0xFFFFu : ((1u << max(npx, 0)) - 1u);
-  uint32_t m = 0u;
-#pragma unroll
-  for (int i = 0; i < 16; ++i)
-    if (k[i] != kEmpty) m |= 1u << i;
-  m &= rowmask;
-  const uint32_t holes = ~m & rowmask;
-  if (!__any_sync(0xffffffffu, holes != 0u)) return holes;
-
-  const int first = m ? x0 + __ffs(m) - 1 : kNoTarget;  // this chunk's first / last filled target
-  const int last = m ? x0 + 31 - __clz(m) : -1;
-  // holes before the chunk's first filled target need the key carried in from the left,
-  // holes after its last one the key carried in from the right
-  const uint32_t before = m ? holes & ((1u << (first - x0)) - 1u) : holes;
-  const uint32_t after = m ? holes & ~((2u << (last - x0)) - 1u) : holes;
-  const uint32_t lanes = __ballot_sync(0xffffffffu, m != 0u);
-  const uint32_t lower = lanes & ((1u << lane) - 1u);
-  const uint32_t upper = lanes & ~((2u << lane) - 1u);
-  int nl = __shfl_sync(0xffffffffu, last, lower ? 31 - __clz(lower) : lane);
-  int nr = __shfl_sync(0xffffffffu, first, upper ? __ffs(upper) - 1 : lane);
-  if (!lower) nl = -1;
-  if (!upper) nr = kNoTarget;
-  if (__any_sync(0xffffffffu, before && !lower)) {
-    const int w = warp_lo > 0 ? warp_walk_left(zb, warp_lo - 1, lane) : -1;
-    if (!lower) nl = w;
-  }
-  if (__any_sync(0xffffffffu, after && !upper)) {
-    const int w = warp_hi < W ? warp_walk_right(zb, warp_hi, W, lane) : kNoTarget;
-    if (!upper) nr = w;
-  }
-  // left to right: every hole takes the last filled key (entries past the row's end take
-  // whatever they take: they are never stored and this sweep carries nothing leftwards)
-  uint32_t c = nl >= 0 ? lds_u32(zs + 4u * nl) : kEmpty;
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (k[j] != kEmpty) c = k[j];
-    k[j] = c;
-  }
-  // right to left: a hole keeps the right key where it is strictly farther
-  c = nr < W ? lds_u32(zs + 4u * nr) : 0u;
-#pragma unroll
-  for (int j = 15; j >= 0; --j) {
-    if ((m >> j) & 1u) c = k[j];
-    else if (c > (k[j] | 0xFFFFFFu)) k[j] = c;
-  }
-  // holes before the first filled target of the row: the right key, or the input pixel
-  // when the row has no filled target at all
-  const bool row_start = nl < 0 && before != 0u;
-  if (__any_sync(0xffffffffu, row_start) && row_start) {
-    const int r = m ? first : nr;
-    if (r < W) {
-      const uint32_t cr = lds_u32(zs + 4u * r);
-#pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if ((before >> j) & 1u) k[j] = cr;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j)  // (no bit is set past the row's end)
-        if ((before >> j) & 1u) k[j] = rgb_at_global(grow, x0 + j);
-    }
-  }
-  return holes;
 }
 
 // Rounded-up per-byte mean of two packed colours: (a + b + 1) >> 1 in every byte.
@@ -340,8 +254,10 @@ __device__ __forceinline__ void store_bytes(uint8_t *p, const uint32_t (&w)[N], 
     if (b < nbytes) p[b] = static_cast<uint8_t>(bsel(w, b));
 }
 
-__device__ __forceinline__ void store48(uint8_t *p, const uint32_t (&w)[12], int npx) {
-  if (npx == 16 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+// 16 packed colours (48 bytes) at p: three 16-byte stores when the chunk is whole and
+// the row 16-byte aligned (`fast`), else byte stores of the npx pixels.
+__device__ __forceinline__ void store48(uint8_t *p, const uint32_t (&w)[12], int npx, bool fast) {
+  if (fast) {
     uint4 *q = reinterpret_cast<uint4 *>(p);
     q[0] = make_uint4(w[0], w[1], w[2], w[3]);
     q[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -371,6 +287,44 @@ __device__ __forceinline__ void store16(uint8_t *p, uint4 v, int npx) {
   }
 }
 
+// A red.shared.min at a + OFF when pred holds (no branch).
+template <int OFF>
+__device__ __forceinline__ void reds_min_at_if(uint32_t a, uint32_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.u32 p, %2, 0;\n\t"
+      "@p red.shared.min.u32 [%0+%3], %1;\n\t}" ::"r"(a),
+      "r"(v), "r"(static_cast<uint32_t>(pred)), "n"(OFF)
+      : "memory");
+}
+
+// Four consecutive 32-column steps G*4 .. G*4+3 of a lane's sources in the forward warp:
+// 255 - depth from the depth row (ds), colour words from the input row (cws, the colour
+// at bit offset sh), the two target offsets from the table (ls), atomics into the left
+// (bl) and right (br) z-buffers at the sources' own columns plus the offsets.  All
+// shared loads come before the atomics.
+template <int G>
+__device__ __forceinline__ void scatter4(uint32_t ds, uint32_t cws, uint32_t sh, uint32_t ls, uint32_t bl,
+                                         uint32_t br) {
+  uint32_t fv[4], cw[8];
+  lds_u8_step32x4(ds + 128 * G, fv);
+  lds_u32_pair_step96x4(cws + 384 * G, cw);
+  uint2 lt[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) lt[j] = lds_u32x2(ls + 8u * fv[j]);
+  uint32_t e[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) e[j] = __byte_perm(__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh), fv[j], 0x4210);
+  reds_min_at<128 * (4 * G + 0)>(bl + lt[0].x, e[0]);
+  reds_min_at<128 * (4 * G + 0)>(br + lt[0].y, e[0]);
+  reds_min_at<128 * (4 * G + 1)>(bl + lt[1].x, e[1]);
+  reds_min_at<128 * (4 * G + 1)>(br + lt[1].y, e[1]);
+  reds_min_at<128 * (4 * G + 2)>(bl + lt[2].x, e[2]);
+  reds_min_at<128 * (4 * G + 2)>(br + lt[2].y, e[2]);
+  reds_min_at<128 * (4 * G + 3)>(bl + lt[3].x, e[3]);
+  reds_min_at<128 * (4 * G + 3)>(br + lt[3].y, e[3]);
+}
+
 // One image's arguments as the band routine sees them (built from the kernel
 // parameters for a single image, from a descriptor in device memory for a batch).
 struct Job {
@@ -383,60 +337,78 @@ struct Job {
   int64_t out_pitch, depth_pitch;
   int W, H, nch, row_bytes, load_mode, nbox, box_bytes, box_step;
   uint32_t outputs;
-  int warp_mode, depth_src, l2_prefetch;
+  int l2_prefetch, fast_store;
 };
 
-// Shared-memory regions of one CTA (laid out for the widest image of the launch).
+// Shared-memory regions of one CTA.
 struct Shm {
-  uint64_t *full;  // ring-slot mbarriers
-  uint64_t *adone; // every warp has stored the next row's depths and cleared its z-buffers
-  uint32_t *lut;   // per depth: -hL in the low 16 bits, -hR in the high 16 bits (two's complement)
-  int32_t *lut_n;  // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
+  uint64_t *full;   // ring-slot mbarriers
+  uint64_t *bdone;  // every warp has scattered the row (B)
+  uint64_t *sdone;  // every warp has published its summary and cleared its targets (C)
+  uint2 *lut;       // per 255 - depth: byte offsets of the left / right targets
+  int32_t *lut_n;   // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
+  uint8_t *wsum;    // [parity][warp][view] uint4 {has, first entry, last entry, 0}
   uint8_t *ring, *drow;
-  uint32_t *zb0;   // [2 rows][L, R][zlen]
-  int nb, srow, zlen;
+  uint32_t zb;      // shared address of the z-buffer region
+  int nb, srow, zlen, zstride, zguard;
 };
 
-__device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch_max, int depth_src) {
-  const BandSmem L = band_smem_layout(nb, srow, nch_max, depth_src);
+__device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch, int nwarps, int zguard) {
+  const BandSmem L = band_smem_layout(nb, srow, nch, nwarps, zguard);
   Shm m;
   m.full = reinterpret_cast<uint64_t *>(smem + L.bar);
-  m.adone = reinterpret_cast<uint64_t *>(smem + L.flags + 8);
-  m.lut = reinterpret_cast<uint32_t *>(smem + L.lut);
+  m.bdone = reinterpret_cast<uint64_t *>(smem + L.flags + 8);
+  m.sdone = reinterpret_cast<uint64_t *>(smem + L.flags + 16);
+  m.lut = reinterpret_cast<uint2 *>(smem + L.lut);
+  m.wsum = smem + L.wsum;
   m.ring = smem + L.ring;
   m.drow = smem + L.drow;
-  m.zb0 = reinterpret_cast<uint32_t *>(smem + L.zb);
+  m.zb = smem_addr(smem + L.zb);
   m.lut_n = reinterpret_cast<int32_t *>(smem + L.zb);
   m.nb = nb;
   m.srow = srow;
-  m.zlen = nch_max * kChunk;
+  m.zlen = nch * kChunk;
+  m.zstride = L.zstride;
+  m.zguard = zguard;
   return m;
 }
 
-// Shift tables into shared memory (all threads; a barrier must follow).
-__device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, const int32_t *lut_n, bool forward) {
+// Shift tables into shared memory (all threads; a barrier must follow).  lut[255 - d] =
+// {4 * (-hL[d]), 4 * (-hR[d])}: a source at column x with depth d lands on target x - h.
+template <bool FWD>
+__device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, const int32_t *lut_n) {
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-    const int32_t h = lut_h[i];
-    const int nl = -static_cast<int16_t>(h & 0xFFFF), nr = -(h >> 16);  // |h| <= 512
-    m.lut[i] = (static_cast<uint32_t>(nr) << 16) | (static_cast<uint32_t>(nl) & 0xFFFFu);
-    if (!forward) m.lut_n[i] = lut_n[i];
+    if (FWD) {
+      const int32_t h = lut_h[255 - i];
+      const int nl = -static_cast<int16_t>(h & 0xFFFF), nr = -(h >> 16);  // |h| <= 512
+      m.lut[i] = make_uint2(static_cast<uint32_t>(4 * nl), static_cast<uint32_t>(4 * nr));
+    } else {
+      m.lut_n[i] = lut_n[i];
+    }
   }
+}
+
+// Every thread's wait on an mbarrier phase, the outcome agreed within the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns) {
+  const bool ok = mbar_wait_bounded(bar, parity, timeout_ns);
+  return __all_sync(kAll, ok);
 }
 
 // Rows [ys, ye) of one image, every stage of the pipeline (see the file comment).  All
 // threads of the CTA call it together.  kbase counts the ring loads this CTA issued
-// before (the slot and mbarrier phase of a load follow from it); it is advanced by the
-// loads issued here.  Returns false when a bounded wait gave up (the status word is
-// set and the copies in flight have been waited for).
+// before (the slot and mbarrier phase of a load follow from it), bph / sph the completed
+// phases of the two per-row mbarriers; all three are advanced here.  Returns false when a
+// bounded wait gave up (the status word is set and the copies in flight have landed).
+template <int DS, bool FWD>
 __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
-                                         uint32_t &abase, int *status, unsigned long long timeout_ns) {
+                                         uint32_t &bph, uint32_t &sph, int *status,
+                                         unsigned long long timeout_ns) {
+  constexpr bool binom = DS == DS_BINOM5;
   const int tid = threadIdx.x, nc = blockDim.x, W = a.W, H = a.H, nb = m.nb;
-  const bool binom = a.depth_src == DS_BINOM5;
-  const bool forward = a.warp_mode == DIBR_WARP_FORWARD;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nc >> 5;
   const int halo = binom ? 2 : 0;
   const int la = max(ys - halo, 0), lb = min(ye + halo, H);
   const int nload = lb - la;
-  const int zimg = a.nch * kChunk;  // this image's targets, rounded up to whole chunks
   const uint32_t k0 = kbase;
   // g / nb as umulhi(g, ceil(2^32 / nb)): exact while g * (nb - 1) < 2^32, far beyond the
   // loads one CTA makes in a launch
@@ -445,57 +417,59 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 
   // Row k = r - la of the band is the (k0 + k)-th load of this CTA: slot (k0+k) % nb.
   // The middle warp issues the loads of rows [issued, upto) (the warps at the row's ends
-  // have the most fill work); the caller guarantees every earlier occupant of those slots
-  // has been released by all threads (a barrier separates the last use from the call).
+  // have the most fill work); every earlier occupant of those slots has been released by
+  // all warps (every warp has scattered it: the bdone mbarrier, or a CTA barrier).
   int issued = 0;
-  const int lw = 32 * ((nc >> 5) >> 1);  // first thread of the loading warp
+  const int lw = 32 * (nwarps >> 1);  // first thread of the loading warp
+  const bool loader = (tid >> 5) == (nwarps >> 1);
   auto issue_loads = [&](int upto) {
     upto = min(upto, nload);
-    if (tid - lw >= 0 && tid - lw < 32) {
-      if (tid == lw && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
-      for (int k = issued; k < upto; ++k) {
-        const uint32_t g = k0 + k;
-        const int s = static_cast<int>(g - ring_div(g) * nb);
-        uint8_t *dst = m.ring + s * m.srow;
-        if (a.load_mode == LM_BULK) {
-          if (tid == lw) {
-            mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.row_bytes));
-            bulk_load(dst, a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes),
-                      &m.full[s]);
-          }
-        } else {
-          if (tid == lw) mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
-          __syncwarp();
-          for (int i = tid - lw; i < a.nbox; i += 32) {
-            if (a.load_mode == LM_T3)
-              tma_load_3d(dst + i * a.box_bytes, a.tmap, 0, i * a.box_step, la + k, &m.full[s]);
-            else
-              tma_load_2d(dst + i * a.box_bytes, a.tmap, i * a.box_step, la + k, &m.full[s]);
-          }
+    if (tid == lw && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
+    for (int k = issued; k < upto; ++k) {
+      const uint32_t g = k0 + k;
+      const int s = static_cast<int>(g - ring_div(g) * nb);
+      uint8_t *dst = m.ring + s * m.srow;
+      if (a.load_mode == LM_BULK) {
+        if (tid == lw) {
+          mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.row_bytes));
+          bulk_load(dst, a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes),
+                    &m.full[s]);
+        }
+      } else {
+        if (tid == lw) mbar_arrive_expect_tx(&m.full[s], static_cast<uint32_t>(a.nbox * a.box_bytes));
+        __syncwarp();
+        for (int i = tid - lw; i < a.nbox; i += 32) {
+          if (a.load_mode == LM_T3)
+            tma_load_3d(dst + i * a.box_bytes, a.tmap, 0, i * a.box_step, la + k, &m.full[s]);
+          else
+            tma_load_2d(dst + i * a.box_bytes, a.tmap, i * a.box_step, la + k, &m.full[s]);
         }
       }
     }
-    issued = max(issued, upto);
+    if (upto > issued) issued = upto;
   };
-  issue_loads(nb);
-  // optionally, the band's later rows go to L2 now
-  if (a.l2_prefetch && tid - lw >= 0 && tid - lw < 32) {
-    if (a.load_mode == LM_BULK) {
-      for (int k = nb + tid - lw; k < nload; k += 32)
-        bulk_prefetch_l2(a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes));
-    } else {
-      for (int j = tid - lw; j < (nload - nb) * a.nbox; j += 32) {
-        const int k = nb + j / a.nbox, i = j % a.nbox;
-        if (a.load_mode == LM_T3) tma_prefetch_3d(a.tmap, 0, i * a.box_step, la + k);
-        else tma_prefetch_2d(a.tmap, i * a.box_step, la + k);
+  if (loader) {
+    issue_loads(nb);
+    // optionally, the band's later rows go to L2 now
+    if (a.l2_prefetch) {
+      if (a.load_mode == LM_BULK) {
+        for (int k = nb + lane; k < nload; k += 32)
+          bulk_prefetch_l2(a.in + static_cast<int64_t>(la + k) * a.in_pitch, static_cast<uint32_t>(a.row_bytes));
+      } else {
+        for (int j = lane; j < (nload - nb) * a.nbox; j += 32) {
+          const int k = nb + j / a.nbox, i = j % a.nbox;
+          if (a.load_mode == LM_T3) tma_prefetch_3d(a.tmap, 0, i * a.box_step, la + k);
+          else tma_prefetch_2d(a.tmap, i * a.box_step, la + k);
+        }
       }
     }
   }
 
-  const int lane = tid & 31;
   const int x0 = tid * kChunk;
   const int npx = max(0, min(kChunk, W - x0));
   const bool active = npx > 0;
+  const bool own_chunk = tid < a.nch;            // the thread's chunk exists (active or not)
+  const int x0c = min(x0, (a.nch - 1) * kChunk);  // clamped: loads stay inside the buffers
   const int warp_lo = (tid & ~31) * kChunk;
   const int warp_hi = min(W, warp_lo + 32 * kChunk);
   bool timed_out = false;
@@ -505,8 +479,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   };
   auto wait_row = [&](int r) {
     const uint32_t g = k0 + (r - la), q = ring_div(g);
-    if (!mbar_wait_bounded(&m.full[g - q * nb], q & 1, timeout_ns)) timed_out = true;
+    if (!warp_wait(&m.full[g - q * nb], q & 1, timeout_ns)) timed_out = true;
   };
+  // shared address of target 0 of the z-buffer row of parity p, view v
+  auto zrow = [&](int p, int v) { return m.zb + 4u * static_cast<uint32_t>(m.zguard + (2 * p + v) * m.zstride); };
 
   const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
   const bool want_holes = (a.outputs & DIBR_OUT_HOLES) != 0;
@@ -514,8 +490,15 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   const bool want_l = (a.outputs & DIBR_OUT_LEFT) != 0;
   const bool want_r = (a.outputs & DIBR_OUT_RIGHT) != 0;
   const bool want_hsbs = (a.outputs & DIBR_OUT_HSBS) != 0;
-  bool aborted = false;
 
+  // every z-buffer target empty (later rows: C clears its targets once it has read them)
+  if (FWD) {
+    const uint4 e = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    for (int i = tid; 4 * i < m.zlen; i += nc) {  // groups of 4 targets
+#pragma unroll
+      for (int r = 0; r < 4; ++r) sts_u32x4(zrow(r >> 1, r & 1) + 16u * i, e);
+    }
+  }
   VCascade vc;
   vc.clear();
   if (binom) {
@@ -525,157 +508,233 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 #pragma unroll 1
     for (int i = -2; i <= 1; ++i) {
       const int r = min(max(ys + i, 0), H - 1);
-      uint32_t yq[10] = {0u}, V[10];
-      if (active) luma20(slot(r), x0, W, yq);
+      uint32_t yq[10], V[10];
+      luma20(slot(r), x0c, W, yq);
       vc.feed(yq, V);
     }
-    if (consumer_sync_or(timed_out, nc)) aborted = true;
-    else issue_loads((ys - la) + nb);  // the rows above the band are done with
   }
+  // the cleared z-buffers (and, with the binomial, the rows above the band) are done with
+  bool aborted = consumer_sync_or(timed_out, nc);
+  if (!aborted && loader) issue_loads((ys - la) + nb);
 
-  // Per row, three phases: A (depth of the row into shared memory, its z-buffers cleared),
-  // B (the forward warp: every source's entry reduced into the z-buffers), C (winners, hole
-  // fill, formatting, stores).  B of a row needs A of that row done by every warp (a split
-  // barrier: each warp arrives after its A and waits before its B), and C of a row needs B
-  // of that row done by every warp (a full barrier).  A of the next row comes before C of
-  // this one, so a warp that finishes C early scatters the next row while the others still
-  // resolve this one.  C reads this row's input from global memory (the rare cases that
-  // need it), so its ring slot is refilled as soon as B of the row is done.
+  const uint32_t ltm = lanemask_lt(), gtm = lanemask_gt();
+
+  // ---- A: the depth of row y (registers, 4 per word), 255 - depth into the depth row
   auto phase_a = [&](int y) -> uint4 {
-    uint4 d = make_uint4(0u, 0u, 0u, 0u);
-    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
-    uint32_t *zr = zl + m.zlen;
+    uint4 d;
     if (binom) {
       const int r2 = y + 2;
       if (r2 < lb) wait_row(r2);
       uint32_t V[10];
       if (r2 < H) {
-        uint32_t yq[10] = {0u};
-        if (active) luma20(slot(r2), x0, W, yq);
+        uint32_t yq[10];
+        luma20(slot(r2), x0c, W, yq);
         vc.feed(yq, V);
       } else {
         vc.feed_repeat(V);  // rows below the image repeat row H-1
       }
       d = binom_h(V);
-    } else {
+    } else if (DS == DS_LUMA) {
       wait_row(y);
+      d = luma16(slot(y), x0c);
+    } else {
+      wait_row(y);  // B reads the row's colours
+      d = make_uint4(0u, 0u, 0u, 0u);
       if (active) {
-        if (a.depth_src == DS_LUMA) {
-          const uint8_t *row = slot(y);
-          uint32_t w[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-          for (int j = 0; j < 16; ++j) w[j >> 2] |= luma_px(rgb_at(row, min(x0 + j, W - 1))) << (8 * (j & 3));
-          d = make_uint4(w[0], w[1], w[2], w[3]);
+        const uint8_t *dp = a.depth_in + static_cast<int64_t>(y) * a.depth_in_pitch + x0;
+        if (npx == kChunk && (reinterpret_cast<uintptr_t>(dp) & 15u) == 0) {
+          d = *reinterpret_cast<const uint4 *>(dp);
         } else {
-          const uint8_t *dp = a.depth_in + static_cast<int64_t>(y) * a.depth_in_pitch + x0;
-          if (npx == kChunk && (reinterpret_cast<uintptr_t>(dp) & 15u) == 0) {
-            d = *reinterpret_cast<const uint4 *>(dp);
-          } else {
-            uint32_t w[4] = {0u, 0u, 0u, 0u};
-            for (int i = 0; i < npx; ++i) w[i >> 2] |= static_cast<uint32_t>(dp[i]) << (8 * (i & 3));
-            d = make_uint4(w[0], w[1], w[2], w[3]);
-          }
+          uint32_t w[4] = {0u, 0u, 0u, 0u};
+          for (int i = 0; i < npx; ++i) w[i >> 2] |= static_cast<uint32_t>(dp[i]) << (8 * (i & 3));
+          d = make_uint4(w[0], w[1], w[2], w[3]);
         }
       }
     }
-    if (active && want_depth)
-      store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d, npx);
-    if (forward) {
-      if (active) *reinterpret_cast<uint4 *>(m.drow + x0) = d;
-      // clear this warp's 512 targets of both views, consecutive lanes on consecutive
-      // 16-byte words (no bank conflicts)
-      const uint4 e = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    if (want_depth && active) store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d, npx);
+    if (FWD && own_chunk) *reinterpret_cast<uint4 *>(m.drow + x0) = make_uint4(~d.x, ~d.y, ~d.z, ~d.w);
+    return d;
+  };
+
+  // ---- B: the forward warp of row y: the warp's 512 sources, consecutive lanes on
+  // consecutive columns, so that the atomics of one instruction land on distinct banks
+  // (shifts vary slowly); all shared loads of four steps are issued before their atomics
+  auto phase_b = [&](int y) {
+    if (!FWD) return;
+    const int xb = warp_lo + lane;
+    const uint32_t ob = 3u * static_cast<uint32_t>(xb);
+    const uint32_t cws = smem_addr(slot(y)) + (ob & ~3u);  // the lane's colours: +96 bytes per step
+    const uint32_t sh = (ob & 3u) * 8u;
+    const uint32_t ds = smem_addr(m.drow) + static_cast<uint32_t>(xb);
+    const uint32_t ls = smem_addr(m.lut);
+    const int p = y & 1;
+    const uint32_t bl = zrow(p, 0) + 4u * static_cast<uint32_t>(xb);
+    const uint32_t br = zrow(p, 1) + 4u * static_cast<uint32_t>(xb);
+    if (warp_hi - warp_lo == 32 * kChunk) {
+      scatter4<0>(ds, cws, sh, ls, bl, br);
+      scatter4<1>(ds, cws, sh, ls, bl, br);
+      scatter4<2>(ds, cws, sh, ls, bl, br);
+      scatter4<3>(ds, cws, sh, ls, bl, br);
+    } else {
+      // the row's last, partial warp: columns from warp_hi on do not exist (their loads
+      // read column warp_hi - 1, so that they stay in the row; their atomics are skipped)
+      const uint32_t rs = smem_addr(slot(y)), dr = smem_addr(m.drow);
+      const int ng = (warp_hi - warp_lo + 127) >> 7;  // groups of 4 x 32 columns holding some
+#pragma unroll 1
+      for (int g = 0; g < ng; ++g) {
+        uint32_t fv[4], cw[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t xc = static_cast<uint32_t>(min(xb + 32 * (4 * g + j), warp_hi - 1));
+          const uint32_t ca = rs + ((3u * xc) & ~3u);
+          fv[j] = lds_u8(dr + xc);
+          cw[2 * j] = lds_u32(ca);
+          cw[2 * j + 1] = lds_u32(ca + 4);
+        }
+        uint2 lt[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lt[j] = lds_u32x2(ls + 8u * fv[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = xb + 32 * (4 * g + j) < warp_hi;
+          const uint32_t e = __byte_perm(__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh), fv[j], 0x4210);
+          const uint32_t off = 512u * static_cast<uint32_t>(g) + 128u * j;
+          reds_min_at_if<0>(bl + off + lt[j].x, e, in);
+          reds_min_at_if<0>(br + off + lt[j].y, e, in);
+        }
+      }
+    }
+  };
+  auto arrive_b = [&]() {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(m.bdone);
+  };
+
+  // ---- C: row y's targets: winners, hole fill, formatting, stores
+  auto wsum_at = [&](int p, int w, int v) { return smem_addr(m.wsum) + 16u * static_cast<uint32_t>((p * nwarps + w) * 2 + v); };
+  auto phase_c = [&](int y, uint4 d) {
+    // every warp has scattered row y: its targets are final and its ring slot is free
+    if (!warp_wait(m.bdone, (bph + static_cast<uint32_t>(y - ys)) & 1u, timeout_ns)) timed_out = true;
+    if (loader) issue_loads((y - la) + 1 + nb);
+    const uint8_t *grow = a.in + static_cast<int64_t>(y) * a.in_pitch;
+    const int p = y & 1;
+    uint32_t k[2][16];
+    uint32_t hole[2] = {0u, 0u};
+    if (FWD) {
+      const uint32_t rowmask = npx >= kChunk ? 0xFFFFu : ((1u << npx) - 1u);
+      uint32_t mm[2], fe[2], cl[2], cr[2], lanes[2];
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const uint32_t za = zrow(p, v) + 4u * static_cast<uint32_t>(x0c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 u = lds_u32x4(za + 16u * q);
+          k[v][4 * q] = u.x; k[v][4 * q + 1] = u.y; k[v][4 * q + 2] = u.z; k[v][4 * q + 3] = u.w;
+        }
+        uint32_t mk = 0u;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mk |= (k[v][j] != kEmpty ? 1u : 0u) << j;
+        mk &= rowmask;
+        // the chunk's first and last filled entries, for the neighbouring lanes
+        const int fj = __ffs(mk) - 1, lj = 31 - __clz(mk);
+        fe[v] = lds_u32(za + 4u * static_cast<uint32_t>(fj & 15));
+        const uint32_t le = lds_u32(za + 4u * static_cast<uint32_t>(lj & 15));
+        const uint32_t ln = __ballot_sync(kAll, mk != 0u);
+        const uint32_t lower = ln & ltm, upper = ln & gtm;
+        cl[v] = __shfl_sync(kAll, le, (31 - __clz(lower)) & 31);
+        cr[v] = __shfl_sync(kAll, fe[v], (__ffs(upper) - 1) & 31);
+        const uint32_t wf = __shfl_sync(kAll, fe[v], (__ffs(ln) - 1) & 31);
+        const uint32_t wl = __shfl_sync(kAll, le, (31 - __clz(ln)) & 31);
+        if (lane == 0) sts_u32x4(wsum_at(p, warp, v), make_uint4(ln != 0u ? 1u : 0u, wf, wl, 0u));
+        mm[v] = mk;
+        lanes[v] = ln;
+      }
+      // this warp's targets are read: clear them for row y + 2 (consecutive lanes on
+      // consecutive 16-byte words: no bank conflicts), then tell the other warps that its
+      // summary is published and its targets are clear
+      __syncwarp();
+      const uint4 e4 = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int t = warp_lo + 4 * (32 * q + lane);
-        if (t < zimg) {
-          *reinterpret_cast<uint4 *>(zl + t) = e;
-          *reinterpret_cast<uint4 *>(zr + t) = e;
+        if (t < m.zlen) {
+          sts_u32x4(zrow(p, 0) + 4u * t, e4);
+          sts_u32x4(zrow(p, 1) + 4u * t, e4);
         }
       }
-    }
-    return d;
-  };
-  auto phase_b = [&](int y) {
-    const uint8_t *rgbrow = slot(y);
-    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
-    uint32_t *zr = zl + m.zlen;
-    if (forward) {
-      // the warp's 512 sources, consecutive lanes on consecutive columns, so that the
-      // atomics of one instruction land on distinct banks (shifts vary slowly)
-      const int xb = warp_lo + lane;
-      const uint32_t ob = 3u * static_cast<uint32_t>(xb);
-      const uint32_t cws = smem_addr(rgbrow) + (ob & ~3u);  // the lane's colours: +96 bytes per step
-      const uint32_t sh = (ob & 3u) * 8u;
-      const uint32_t ds = smem_addr(m.drow) + static_cast<uint32_t>(xb);
-      const uint32_t ls = smem_addr(m.lut);
-      const uint32_t zls = smem_addr(zl), zrs = smem_addr(zr);
-      const bool full_warp = warp_hi - warp_lo == 32 * kChunk;
-      if (full_warp) {
-        // four steps at a time: all their shared loads are issued before their atomics
+      __syncwarp();
+      if (lane == 0) mbar_arrive(m.sdone);
+      // entries from outside the warp, for lanes whose leading (trailing) holes have no
+      // filled target below (above) them in the warp: the nearest warp's last (first)
+      // filled entry, from the summaries
+      bool need = false;
 #pragma unroll
-        for (int g = 0; g < kChunk / 4; ++g) {
-          uint32_t dv[4], cw[8];
-          lds_u8_step32x4(ds + 128 * g, dv);
-          lds_u32_pair_step96x4(cws + 384 * g, cw);
-          uint32_t lh[4];
+      for (int v = 0; v < 2; ++v) {
+        const uint32_t lower = lanes[v] & ltm, upper = lanes[v] & gtm;
+        need |= active && ((lower == 0u && !(mm[v] & 1u)) || (upper == 0u && !((mm[v] >> ((npx - 1) & 15)) & 1u)));
+      }
+      uint32_t wle[2] = {0u, 0u}, wre[2] = {0u, 0u};
+      bool wlh[2] = {false, false}, wrh[2] = {false, false};
+      if (__any_sync(kAll, need)) {
+        if (!warp_wait(m.sdone, (sph + static_cast<uint32_t>(y - ys)) & 1u, timeout_ns)) timed_out = true;
 #pragma unroll
-          for (int j = 0; j < 4; ++j) lh[j] = lds_u32(ls + 4u * dv[j]);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int x = xb + 32 * (4 * g + j);
-            const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | (~dv[j] << 24);
-            const int tl = x + shift_l(lh[j]), tr = x + shift_r(lh[j]);
-            if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
-            if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+        for (int v = 0; v < 2; ++v) {
+          for (int w = warp - 1; w >= 0; --w) {
+            const uint4 s = lds_u32x4(wsum_at(p, w, v));
+            if (s.x) {
+              wle[v] = s.z;
+              wlh[v] = true;
+              break;
+            }
           }
-        }
-      } else {
-        // the row's last, partial warp: columns from warp_hi on do not exist (their loads
-        // read column warp_hi - 1, so that they stay in the row; their atomics are skipped)
-        const uint32_t rs = smem_addr(rgbrow), dr = smem_addr(m.drow);
-        const int ng = (warp_hi - warp_lo + 127) >> 7;  // groups of 4 x 32 columns holding some
-#pragma unroll 1
-        for (int g = 0; g < ng; ++g) {
-          uint32_t dv[4], cw[8];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t xc = static_cast<uint32_t>(min(xb + 32 * (4 * g + j), warp_hi - 1));
-            const uint32_t ca = rs + ((3u * xc) & ~3u);
-            dv[j] = lds_u8(dr + xc);
-            cw[2 * j] = lds_u32(ca);
-            cw[2 * j + 1] = lds_u32(ca + 4);
-          }
-          uint32_t lh[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) lh[j] = lds_u32(ls + 4u * dv[j]);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int x = xb + 32 * (4 * g + j);
-            if (x < warp_hi) {
-              const uint32_t e = (__funnelshift_r(cw[2 * j], cw[2 * j + 1], sh) & 0xFFFFFFu) | (~dv[j] << 24);
-              const int tl = x + shift_l(lh[j]), tr = x + shift_r(lh[j]);
-              if (static_cast<unsigned>(tl) < static_cast<unsigned>(W)) reds_min(zls + 4u * tl, e);
-              if (static_cast<unsigned>(tr) < static_cast<unsigned>(W)) reds_min(zrs + 4u * tr, e);
+          for (int w = warp + 1; w < nwarps; ++w) {
+            const uint4 s = lds_u32x4(wsum_at(p, w, v));
+            if (s.x) {
+              wre[v] = s.y;
+              wrh[v] = true;
+              break;
             }
           }
         }
       }
-    }
-  };
-  auto phase_c = [&](int y, uint4 d) {
-    uint32_t *zl = m.zb0 + (y & 1) * 2 * m.zlen;
-    uint32_t *zr = zl + m.zlen;
-    const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
-    // this row's input from global memory: its ring slot is refilled while this runs
-    const uint8_t *grow = a.in + static_cast<int64_t>(y) * a.in_pitch;
-    uint32_t kl[16], kr[16];
-    uint32_t hole_l = 0u, hole_r = 0u;
-    if (forward) {
-      hole_l = resolve_view(zl, grow, x0, npx, W, lane, warp_lo, warp_hi, kl);
-      hole_r = resolve_view(zr, grow, x0, npx, W, lane, warp_lo, warp_hi, kr);
+      // Hole fill: a hole shows the winner of the nearest filled target on its farther
+      // side -- of the nearest filled targets to its left and right, the one whose winner
+      // has the smaller depth (the left one on a tie, the only one at a row edge); the
+      // input pixel when the row has no filled target.  Two register sweeps: left to right
+      // carrying the last filled entry into the holes, then right to left carrying the
+      // last filled entry and keeping it where it is strictly farther (entries are
+      // (255 - depth) << 24 | colour, so "c strictly farther than k" is the unsigned
+      // compare c > (k | 0xFFFFFF)).  A missing right entry carries in as 0, which is never
+      // strictly farther; holes with no filled target on their left (the row's start)
+      // carry in the first filled entry on their right from the start.
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const uint32_t lower = lanes[v] & ltm, upper = lanes[v] & gtm, mk = mm[v];
+        const uint32_t rin = upper ? cr[v] : wre[v];
+        const uint32_t lin = lower ? cl[v] : (wlh[v] ? wle[v] : (mk ? fe[v] : rin));
+        uint32_t c = lin;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          c = ((mk >> j) & 1u) ? k[v][j] : c;
+          k[v][j] = c;
+        }
+        c = rin;
+#pragma unroll
+        for (int j = 15; j >= 0; --j) {
+          c = ((mk >> j) & 1u) ? k[v][j] : c;
+          k[v][j] = c > (k[v][j] | 0xFFFFFFu) ? c : k[v][j];
+        }
+        hole[v] = ~mk & rowmask;
+        if (lanes[v] == 0u && !wlh[v] && !wrh[v]) {  // (warp-uniform)
+#pragma unroll
+          for (int j = 0; j < 16; ++j) k[v][j] = active ? rgb_at_global(grow, min(x0 + j, W - 1)) : 0u;
+        }
+      }
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
+      __syncwarp();
+      if (lane == 0) mbar_arrive(m.sdone);
+      const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
       for (int i = 0; i < kChunk; ++i) {
         const int x = min(x0 + i, W - 1);
@@ -683,106 +742,91 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         int sl = (510 * x + n) / 510, sr = (510 * x - n) / 510;
         if (static_cast<unsigned>(sl) >= static_cast<unsigned>(W)) sl = x;
         if (static_cast<unsigned>(sr) >= static_cast<unsigned>(W)) sr = x;
-        kl[i] = active ? rgb_at_global(grow, sl) : 0u;
-        kr[i] = active ? rgb_at_global(grow, sr) : 0u;
+        k[0][i] = active ? rgb_at_global(grow, sl) : 0u;
+        k[1][i] = active ? rgb_at_global(grow, sr) : 0u;
       }
     }
     if (active && want_holes) {
       // one byte per target: bit 0 a hole of the left view, bit 1 of the right view
       auto spread4 = [](uint32_t x) { return ((x & 0xFu) * 0x00204081u) & 0x01010101u; };
       uint4 hv;
-      hv.x = spread4(hole_l) | (spread4(hole_r) << 1);
-      hv.y = spread4(hole_l >> 4) | (spread4(hole_r >> 4) << 1);
-      hv.z = spread4(hole_l >> 8) | (spread4(hole_r >> 8) << 1);
-      hv.w = spread4(hole_l >> 12) | (spread4(hole_r >> 12) << 1);
+      hv.x = spread4(hole[0]) | (spread4(hole[1]) << 1);
+      hv.y = spread4(hole[0] >> 4) | (spread4(hole[1] >> 4) << 1);
+      hv.z = spread4(hole[0] >> 8) | (spread4(hole[1] >> 8) << 1);
+      hv.w = spread4(hole[0] >> 12) | (spread4(hole[1] >> 12) << 1);
       store16(a.out[O_HOLES] + static_cast<int64_t>(y) * a.depth_pitch + x0, hv, npx);
     }
     if (active) {
-      const int64_t ro = static_cast<int64_t>(y) * a.out_pitch;
-      uint32_t w[12];
-      if (want_l) {
-        pack16(kl, w);
-        store48(a.out[O_LEFT] + ro + 3 * x0, w, npx);
-      }
-      if (want_r) {
-        pack16(kr, w);
-        store48(a.out[O_RIGHT] + ro + 3 * x0, w, npx);
-      }
+      const int64_t ro = static_cast<int64_t>(y) * a.out_pitch + 3 * x0;
+      const bool fast = a.fast_store && npx == kChunk;
+      uint32_t wl[12], wr[12];
+      pack16(k[0], wl);
+      pack16(k[1], wr);
+      if (want_l) store48(a.out[O_LEFT] + ro, wl, npx, fast);
+      if (want_r) store48(a.out[O_RIGHT] + ro, wr, npx, fast);
       if (want_ana) {
-        uint32_t c[16];
+        // red from the left view, green and blue from the right: in the packed words the
+        // red bytes are the bytes at offsets 0 mod 3
+        uint32_t wa[12];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) c[i] = __byte_perm(kl[i], kr[i], 0x3650);  // R from L; G, B from R
-        pack16(c, w);
-        store48(a.out[O_ANA] + ro + 3 * x0, w, npx);
+        for (int i = 0; i < 12; ++i) {
+          const uint32_t M = i % 3 == 0 ? 0xFF0000FFu : i % 3 == 1 ? 0x00FF0000u : 0x0000FF00u;
+          wa[i] = (wl[i] & M) | (wr[i] & ~M);
+        }
+        store48(a.out[O_ANA] + ro, wa, npx, fast);
       }
       if (want_hsbs) {
         uint32_t cl8[8], cr8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          cl8[j] = avg_up(kl[2 * j], kl[2 * j + 1]);
-          cr8[j] = avg_up(kr[2 * j], kr[2 * j + 1]);
+          cl8[j] = avg_up(k[0][2 * j], k[0][2 * j + 1]);
+          cr8[j] = avg_up(k[1][2 * j], k[1][2 * j + 1]);
         }
-        uint32_t wl[6], wr[6];
+        uint32_t hl[6], hr[6];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          wl[3 * k] = __byte_perm(cl8[4 * k], cl8[4 * k + 1], 0x4210);
-          wl[3 * k + 1] = __byte_perm(cl8[4 * k + 1], cl8[4 * k + 2], 0x5421);
-          wl[3 * k + 2] = __byte_perm(cl8[4 * k + 2], cl8[4 * k + 3], 0x6542);
-          wr[3 * k] = __byte_perm(cr8[4 * k], cr8[4 * k + 1], 0x4210);
-          wr[3 * k + 1] = __byte_perm(cr8[4 * k + 1], cr8[4 * k + 2], 0x5421);
-          wr[3 * k + 2] = __byte_perm(cr8[4 * k + 2], cr8[4 * k + 3], 0x6542);
+        for (int q = 0; q < 2; ++q) {
+          hl[3 * q] = __byte_perm(cl8[4 * q], cl8[4 * q + 1], 0x4210);
+          hl[3 * q + 1] = __byte_perm(cl8[4 * q + 1], cl8[4 * q + 2], 0x5421);
+          hl[3 * q + 2] = __byte_perm(cl8[4 * q + 2], cl8[4 * q + 3], 0x6542);
+          hr[3 * q] = __byte_perm(cr8[4 * q], cr8[4 * q + 1], 0x4210);
+          hr[3 * q + 1] = __byte_perm(cr8[4 * q + 1], cr8[4 * q + 2], 0x5421);
+          hr[3 * q + 2] = __byte_perm(cr8[4 * q + 2], cr8[4 * q + 3], 0x6542);
         }
         const int np = npx / 2;  // W is even, so chunks hold whole pairs
-        store24(a.out[O_HSBS] + ro + 3 * (x0 / 2), wl, np);
-        store24(a.out[O_HSBS] + ro + 3 * (W / 2 + x0 / 2), wr, np);
+        const int64_t rh = static_cast<int64_t>(y) * a.out_pitch;
+        store24(a.out[O_HSBS] + rh + 3 * (x0 / 2), hl, np);
+        store24(a.out[O_HSBS] + rh + 3 * (W / 2 + x0 / 2), hr, np);
       }
     }
   };
-  // the split barrier: warps arrive after A of a row; it completes once per row
-  auto a_arrive = [&]() {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(m.adone);
-  };
-  auto a_wait = [&]() {
-    if (!mbar_wait_bounded(m.adone, abase & 1u, timeout_ns)) timed_out = true;
-    ++abase;
-  };
 
   uint4 dcur = make_uint4(0u, 0u, 0u, 0u);
-  if (!aborted && ys < ye) {
+  if (!aborted) {
     dcur = phase_a(ys);
-    if (consumer_sync_or(timed_out, nc)) aborted = true;
-    else {
-      phase_b(ys);
-      if (consumer_sync_or(timed_out, nc)) aborted = true;
-    }
+    phase_b(ys);
+    arrive_b();
   }
-  for (int y = ys; y < ye && !aborted; ++y) {
-    // every thread is past B of row y: the slots of rows <= y can be refilled
-    issue_loads((y - la) + 1 + nb);
+  for (int y = ys; y < ye && !aborted && !timed_out; ++y) {
+    // the loader refills the slot of row y as soon as every warp has scattered it
+    if (loader && __any_sync(kAll, mbar_test(m.bdone, (bph + static_cast<uint32_t>(y - ys)) & 1u)))
+      issue_loads((y - la) + 1 + nb);
     const bool more = y + 1 < ye;
     uint4 dnext = make_uint4(0u, 0u, 0u, 0u);
-    if (more) {
-      dnext = phase_a(y + 1);
-      a_arrive();
-    }
+    if (more) dnext = phase_a(y + 1);
     phase_c(y, dcur);
     if (more) {
-      a_wait();
       phase_b(y + 1);
-    }
-    if (consumer_sync_or(timed_out, nc)) {
-      aborted = true;
-      break;
+      arrive_b();
     }
     dcur = dnext;
   }
 
-  kbase = k0 + issued;
+  // every thread agrees whether the band completed
+  aborted = consumer_sync_or(aborted || timed_out, nc);
   if (aborted) {
-    if (tid == 0) {
+    if (tid == lw) {
       atomicOr(status, ST_TIMEOUT_FULL);
-      // let every copy already issued land before the CTA's shared memory goes away
+      // let every copy this CTA issued land before its shared memory goes away
       for (int k = max(0, issued - nb); k < issued; ++k) {
         const uint32_t g = k0 + k;
         if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, timeout_ns)) atomicOr(status, ST_TIMEOUT_DRAIN);
@@ -790,23 +834,32 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     }
     return false;
   }
+  kbase = k0 + static_cast<uint32_t>(nload);
+  bph += static_cast<uint32_t>(ye - ys);
+  sph += static_cast<uint32_t>(ye - ys);
   return true;
 }
 
+__device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nb; ++i) mbar_init(&m.full[i], 1);
+    mbar_init(m.bdone, blockDim.x / 32);
+    mbar_init(m.sdone, blockDim.x / 32);
+    fence_mbar_init();
+  }
+}
+
 // ---------------------------------------------------------------------------------
-// One image: CTA b owns the rows [b*H/grid, (b+1)*H/grid).
+// One image: CTA b owns the rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0.
+template <int DS, bool FWD>
 __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
   // The next launch on the stream may start its set-up while this one runs (programmatic
   // dependent launch); it waits below for this one to complete before any global access.
   griddep_launch_dependents();
   extern __shared__ __align__(128) uint8_t smem[];
-  const Shm m = carve(smem, a.nb, a.srow, a.nch, a.depth_src);
-  fill_luts(m, a.lut_h, a.lut_n, a.warp_mode == DIBR_WARP_FORWARD);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < a.nb; ++i) mbar_init(&m.full[i], 1);
-    mbar_init(m.adone, blockDim.x / 32);
-    fence_mbar_init();
-  }
+  const Shm m = carve(smem, a.nb, a.srow, a.nch, blockDim.x >> 5, a.zguard);
+  fill_luts<FWD>(m, a.lut_h, a.lut_n);
+  init_barriers(m, a.nb);
   __syncthreads();
   // the work before this launch on the stream (whose results may be this launch's inputs,
   // or whose inputs this launch's outputs may overwrite) has completed -- unless the host
@@ -816,25 +869,23 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
   const int nr = a.row1 - a.row0;
   const int ys = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x) * nr / a.grid);
   const int ye = a.row0 + static_cast<int>(static_cast<int64_t>(blockIdx.x + 1) * nr / a.grid);
-  if (ys >= ye) {
-    if (a.overlap) griddep_wait();
-    return;
-  }
-  Job j;
-  j.in = a.in;
-  j.in_pitch = a.in_pitch;
-  j.tmap = &a.tmap;
-  j.depth_in = a.depth_in;
-  j.depth_in_pitch = a.depth_in_pitch;
+  if (ys < ye) {
+    Job j;
+    j.in = a.in;
+    j.in_pitch = a.in_pitch;
+    j.tmap = &a.tmap;
+    j.depth_in = a.depth_in;
+    j.depth_in_pitch = a.depth_in_pitch;
 #pragma unroll
-  for (int i = 0; i < O_COUNT; ++i) j.out[i] = a.out[i];
-  j.out_pitch = a.out_pitch;
-  j.depth_pitch = a.depth_pitch;
-  j.W = a.W; j.H = a.H; j.nch = a.nch; j.row_bytes = a.row_bytes; j.load_mode = a.load_mode;
-  j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
-  j.outputs = a.outputs; j.warp_mode = a.warp_mode; j.depth_src = a.depth_src; j.l2_prefetch = a.l2_prefetch;
-  uint32_t kbase = 0, abase = 0;
-  run_band(j, m, ys, ye, kbase, abase, a.status, a.timeout_ns);
+    for (int i = 0; i < O_COUNT; ++i) j.out[i] = a.out[i];
+    j.out_pitch = a.out_pitch;
+    j.depth_pitch = a.depth_pitch;
+    j.W = a.W; j.H = a.H; j.nch = a.nch; j.row_bytes = a.row_bytes; j.load_mode = a.load_mode;
+    j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
+    j.outputs = a.outputs; j.l2_prefetch = a.l2_prefetch; j.fast_store = a.fast_store;
+    uint32_t kbase = 0, bph = 0, sph = 0;
+    run_band<DS, FWD>(j, m, ys, ye, kbase, bph, sph, a.status, a.timeout_ns);
+  }
   if (a.overlap) griddep_wait();
 }
 
@@ -847,14 +898,12 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
   // frees while its last units finish, instead of waiting for the last of them.
   griddep_launch_dependents();
   extern __shared__ __align__(128) uint8_t smem[];
-  int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, DS_BINOM5).flags);
-  const Shm m = carve(smem, b.nb, b.srow, b.nch_max, DS_BINOM5);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < b.nb; ++i) mbar_init(&m.full[i], 1);
-    mbar_init(m.adone, blockDim.x / 32);
-    fence_mbar_init();
-  }
-  uint32_t kbase = 0, abase = 0;
+  const int nwarps = blockDim.x >> 5;
+  // the barriers and the unit word sit at the same place in every image's layout
+  const Shm m0 = carve(smem, b.nb, b.srow, b.nch_max, nwarps, b.zguard);
+  int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, nwarps, b.zguard).flags);
+  init_barriers(m0, b.nb);
+  uint32_t kbase = 0, bph = 0, sph = 0;
   while (true) {
     __syncthreads();  // the previous unit is done with the ring, tables and unit_s
     if (threadIdx.x == 0) *unit_s = atomicAdd(b.counter, 1);
@@ -863,6 +912,9 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     if (u >= b.n_units) break;
     const int4 un = b.units[u];  // {image, first row, end row}
     const ImageDesc &dsc = b.descs[un.x];
+    // this image's layout (its z-buffer rows as wide as its own row, so that its targets
+    // past the row's end are the ones its C clears)
+    const Shm m = carve(smem, b.nb, b.srow, dsc.nch, nwarps, b.zguard);
     Job j;
     j.in = dsc.in;
     j.in_pitch = dsc.in_pitch;
@@ -875,31 +927,47 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     j.depth_pitch = dsc.depth_pitch;
     j.W = dsc.W; j.H = dsc.H; j.nch = dsc.nch; j.row_bytes = dsc.row_bytes; j.load_mode = LM_BULK;
     j.nbox = 1; j.box_bytes = dsc.row_bytes; j.box_step = 0;
-    j.outputs = dsc.outputs; j.warp_mode = dsc.warp_mode; j.depth_src = dsc.depth_src; j.l2_prefetch = 0;
-    fill_luts(m, dsc.lut_h, dsc.lut_n, j.warp_mode == DIBR_WARP_FORWARD);
+    j.outputs = dsc.outputs; j.l2_prefetch = 0;
+    j.fast_store = ((reinterpret_cast<uintptr_t>(dsc.out[O_ANA]) | reinterpret_cast<uintptr_t>(dsc.out[O_LEFT]) |
+                     reinterpret_cast<uintptr_t>(dsc.out[O_RIGHT]) | static_cast<uintptr_t>(dsc.out_pitch)) & 15u) == 0;
+    const bool fwd = dsc.warp_mode == DIBR_WARP_FORWARD;
+    if (fwd) fill_luts<true>(m, dsc.lut_h, dsc.lut_n);
+    else fill_luts<false>(m, dsc.lut_h, dsc.lut_n);
     __syncthreads();
-    if (!run_band(j, m, un.y, un.z, kbase, abase, b.status, b.timeout_ns)) break;
+    bool ok;
+    switch (dsc.depth_src * 2 + (fwd ? 0 : 1)) {
+      case DS_BINOM5 * 2: ok = run_band<DS_BINOM5, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      case DS_BINOM5 * 2 + 1: ok = run_band<DS_BINOM5, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      case DS_LUMA * 2: ok = run_band<DS_LUMA, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      case DS_LUMA * 2 + 1: ok = run_band<DS_LUMA, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      case DS_GLOBAL * 2: ok = run_band<DS_GLOBAL, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      default: ok = run_band<DS_GLOBAL, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+    }
+    if (!ok) break;
   }
   // A chained launch's CTAs wait for the previous launch to complete before they exit, so
   // that the work after the batch in stream order still follows all of it.
   griddep_wait();
 }
 
+// The dynamic shared-memory limit of a kernel is raised once per device (the attribute
+// is per function and device); bit d of `done` records device d.
 template <typename K>
-cudaError_t allow_smem(K kernel, bool &done) {
-  if (done) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (e == cudaSuccess) done = true;
+cudaError_t allow_smem(K kernel, std::atomic<uint64_t> &done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
 
-}  // namespace
-
-
-cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
-  (void)ctas_per_sm;
-  static bool done = false;  // per process: the attribute is per function
-  cudaError_t e = allow_smem(band_kernel, done);
+template <int DS, bool FWD>
+cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
+  static std::atomic<uint64_t> done{0};
+  cudaError_t e = allow_smem(band_kernel<DS, FWD>, done);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.grid);
@@ -911,12 +979,24 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, band_kernel, a);
+  e = cudaLaunchKernelEx(&cfg, band_kernel<DS, FWD>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
+  (void)ctas_per_sm;
+  const bool fwd = a.warp_mode == DIBR_WARP_FORWARD;
+  switch (a.depth_src) {
+    case DS_BINOM5: return fwd ? launch_band_t<DS_BINOM5, true>(a, smem_bytes, st) : launch_band_t<DS_BINOM5, false>(a, smem_bytes, st);
+    case DS_LUMA: return fwd ? launch_band_t<DS_LUMA, true>(a, smem_bytes, st) : launch_band_t<DS_LUMA, false>(a, smem_bytes, st);
+    default: return fwd ? launch_band_t<DS_GLOBAL, true>(a, smem_bytes, st) : launch_band_t<DS_GLOBAL, false>(a, smem_bytes, st);
+  }
+}
+
 cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {
-  static bool done = false;
+  static std::atomic<uint64_t> done{0};
   cudaError_t e = allow_smem(batch_kernel, done);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

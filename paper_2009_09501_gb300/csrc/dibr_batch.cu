@@ -25,6 +25,17 @@ dibr_status check_image_args(const dibr_params *p, const dibr_image *img, const 
 void shift_tables(const dibr_params *p, int32_t *lut_h, int32_t *lut_n);
 }  // namespace dibr
 
+// The z-buffer guard every image of a batch fits in: the largest shift of their tables.
+static int batch_zguard(const dibr_params *p, int n_params) {
+  int g = 4;
+  for (int i = 0; i < n_params; ++i) {
+    int32_t lh[256], ln[256];
+    shift_tables(&p[i], lh, ln);
+    g = std::max(g, zguard_of(lh));
+  }
+  return g;
+}
+
 void dibr_ctx::release_batch_buffers() {
   for (DevBuf *b : {&batch_desc, &batch_img, &batch_depth}) {
     dev_free(b->ptr);
@@ -54,7 +65,7 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
                                            const dibr_outputs *outs) {
   if (n == 0) return DIBR_OK;
   std::vector<int> own, shared;
-  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm};
+  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm, batch_zguard(p, n_params)};
   for (int i = 0; i < n; ++i) {
     const int w = imgs[i].width, rb = round_up(3 * w, 16);
     int cl = 0;
@@ -151,7 +162,7 @@ dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_
     heights[i] = imgs[i].height;
   }
   BatchClass cls[kMaxClasses];
-  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm};
+  const BatchLimits lim{max_smem, smem_per_sm, tuning.ring_slots, tuning.ctas_per_sm, batch_zguard(p, n_params)};
   const int nclass = plan_batch_classes(n, widths.data(), row_bytes.data(), lim, class_of.data(), cls);
   if (nclass < 1) {
     set_error("batch images too wide for shared memory");
@@ -236,6 +247,7 @@ dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_
     b.srow = cls[c].srow;
     b.nch_max = cls[c].nch_max;
     b.nc = cls[c].nc;
+    b.zguard = lim.zguard;
     const int grid = std::max(1, std::min(cls[c].n_units, num_sms * cls[c].per));
     e = launch_batch(b, grid, cls[c].smem, c > 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");

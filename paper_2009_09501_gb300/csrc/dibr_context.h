@@ -77,8 +77,8 @@ struct dibr_ctx {
   void *dev_alloc(size_t bytes);
   void dev_free(void *p);
   dibr_status ensure(dibr::DevBuf &b, size_t bytes);
-  dibr_status plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, dibr::BandArgs &a,
-                        int &smem, int &per_sm);
+  dibr_status plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, int zguard,
+                        dibr::BandArgs &a, int &smem, int &per_sm);
   dibr_status encode_input(dibr::BandArgs &a, const uint8_t *dev_rgb, int64_t pitch);
   dibr_status enqueue_device(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);
   dibr_status synthesize_staged(const dibr_image *img, const dibr_params *p, const dibr_outputs *o);

@@ -75,6 +75,7 @@ struct BandArgs {
   int32_t nb;        // ring slots
   int32_t nch;       // 16-pixel chunks per row
   int32_t nc;        // threads per CTA, one 16-pixel chunk each (multiple of 32)
+  int32_t zguard;    // guard targets on each side of a z-buffer row (>= the largest shift)
   int32_t grid;      // CTAs; CTA b owns rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0
   int32_t row0, row1;  // the rows this launch computes (all of them: 0, H)
   int32_t overlap;   // 1: independent of the previous launch on the stream (start at once;
@@ -82,6 +83,7 @@ struct BandArgs {
   uint32_t outputs;  // DIBR_OUT_* bits
   int32_t warp_mode; // DIBR_WARP_*
   int32_t depth_src; // DepthSource
+  int32_t fast_store;  // every RGB output base and the output pitch are 16-byte aligned
   int *status;
   unsigned long long timeout_ns;
   int32_t lut_h[256];  // low 16 bits: hL[d], high 16 bits: hR[d] (signed)
@@ -89,27 +91,47 @@ struct BandArgs {
 };
 
 // Shared-memory layout of the band kernel (bytes from the dynamic smem base).
+//   bar   ring-slot mbarriers full[kMaxRing]
+//   flags +0: the batch's current work unit; +8, +16: the per-row mbarriers (every warp
+//         has scattered the row / has read and cleared its targets of the row)
+//   lut   uint2 per value of 255 - depth: byte offsets of the left / right target
+//   wsum  per row parity, warp and view: {has a filled target, first, last filled entry}
+//   ring  input rows;  drow  255 - depth of the current row, one byte per column
+//   zb    z-buffers, [parity][view] rows of zlen targets separated by zguard guard targets
+//         (targets a shift moves outside the row land in a guard and are never read);
+//         the literal gather keeps int32 lut_n[256] here instead
 struct BandSmem {
-  int bar, flags, lut, ring, drow, zb, total;
+  int bar, flags, lut, wsum, ring, drow, zb, zstride, total;
 };
 
 __host__ __device__ inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-__host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, int depth_src) {
-  (void)depth_src;
+__host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, int nwarps, int zguard) {
   BandSmem s;
-  s.bar = 0;                       // full[kMaxRing] mbarriers
-  s.flags = 8 * kMaxRing;          // batched launches: the current work unit
-  s.lut = s.flags + 64;            // uint32 lut[256]: -hL[d] | -hR[d] << 16
-  s.ring = round_up(s.lut + 1024, 128);
-  // depth of the current row, one byte per column (read back by the scatter)
+  s.bar = 0;
+  s.flags = 8 * kMaxRing;
+  s.lut = s.flags + 64;
+  s.wsum = s.lut + 2048;
+  s.ring = round_up(s.wsum + 2 * nwarps * 2 * 16, 128);
   s.drow = round_up(s.ring + nb * srow, 16);
-  // z-buffers of the forward warp, double buffered across rows: [2][L, R][nch * 16]
-  // (the literal gather keeps lut_n[256] here instead)
   s.zb = round_up(s.drow + nch * kChunk, 16);
-  const int zbytes = 4 * nch * kChunk * 4;
+  const int zlen = nch * kChunk;  // a multiple of 16 targets: rows stay 16-byte aligned
+  s.zstride = zlen + zguard;      // words from one row's target 0 to the next row's
+  const int zbytes = 4 * (4 * zlen + 5 * zguard);
   s.total = s.zb + (zbytes > 1024 ? zbytes : 1024);
   return s;
+}
+
+// Guard targets on each side of a z-buffer row for the shift tables lut_h (low / high 16
+// bits: hL, hR): the largest |h|, rounded up to whole 16-byte groups.
+inline int zguard_of(const int32_t *lut_h) {
+  int g = 0;
+  for (int d = 0; d < 256; ++d) {
+    const int hl = static_cast<int16_t>(lut_h[d] & 0xFFFF), hr = lut_h[d] >> 16;
+    g = g > (hl < 0 ? -hl : hl) ? g : (hl < 0 ? -hl : hl);
+    g = g > (hr < 0 ? -hr : hr) ? g : (hr < 0 ? -hr : hr);
+  }
+  return round_up(g + 1, 4);
 }
 
 // One image of a batched launch, in device memory.
@@ -138,7 +160,7 @@ struct BatchArgs {
   int *counter;
   int *status;
   unsigned long long timeout_ns;
-  int32_t nb, srow, nch_max, nc;
+  int32_t nb, srow, nch_max, nc, zguard;
 };
 
 // ---- planning a batch (host; no allocation, so the no-allocation entry point shares it)
@@ -164,6 +186,7 @@ struct BatchClass {
 struct BatchLimits {
   int max_smem, smem_per_sm;  // device limits
   int ring_slots, ctas_per_sm;  // tuning caps (0: none)
+  int zguard;                   // z-buffer guard of every image of the batch (the largest)
 };
 
 inline int chunks_of(int width) { return (width + kChunk - 1) / kChunk; }
@@ -202,7 +225,7 @@ inline int plan_batch_classes(int n, const int *width, const int *row_bytes, con
     const int max_per = by_regs < by_threads ? by_regs : by_threads;
     k.per = 0;
     for (int nb = 4; nb <= max_nb; ++nb) {
-      const int tot = band_smem_layout(nb, k.srow, k.nch_max, DS_BINOM5).total;
+      const int tot = band_smem_layout(nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
       if (tot > lim.max_smem) continue;
       int per = lim.smem_per_sm / (tot + 1024);
       if (per > max_per) per = max_per;
@@ -213,7 +236,7 @@ inline int plan_batch_classes(int n, const int *width, const int *row_bytes, con
       }
     }
     if (k.per < 1) return -1;
-    k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, DS_BINOM5).total;
+    k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
   }
   return nclass;
 }

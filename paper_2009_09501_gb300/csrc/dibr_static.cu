@@ -122,7 +122,15 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
   // one launch per group of equal block width (the context's batched launch plan)
   BatchClass cls[kMaxClasses];
   int class_of[kStaticMaxImages], order[kStaticMaxImages];
-  const BatchLimits lim{d.max_smem, d.smem_per_sm, 0, 0};
+  // the z-buffer guard every image fits in: the largest shift of their tables
+  int zguard = 4;
+  for (int i = 0; i < n_params; ++i) {
+    int32_t lh[256], ln[256];
+    shift_tables(&p[i], lh, ln);
+    const int g = zguard_of(lh);
+    if (g > zguard) zguard = g;
+  }
+  const BatchLimits lim{d.max_smem, d.smem_per_sm, 0, 0, zguard};
   const int nclass = plan_batch_classes(n, widths, row_bytes, lim, class_of, cls);
   if (nclass < 1) return DIBR_E_INVALID;
   order_by_area(n, widths, heights, order);
@@ -190,6 +198,7 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     b.srow = cls[c].srow;
     b.nch_max = cls[c].nch_max;
     b.nc = cls[c].nc;
+    b.zguard = zguard;
     const int grid = cls[c].n_units < d.sms * cls[c].per ? cls[c].n_units : d.sms * cls[c].per;
     e = launch_batch(b, grid > 0 ? grid : 1, cls[c].smem, c > 0, stream);
     if (e != cudaSuccess) return DIBR_E_CUDA;
