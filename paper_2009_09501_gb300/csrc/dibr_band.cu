@@ -115,7 +115,7 @@ __device__ __forceinline__ void luma20(const uint8_t *row, int x0, int W, uint32
   }
   // clamp to the row: the columns before 0 and after W-1 take column 0 and column W-1
   // (window column j sits in word 2 * (j / 4) + j % 2, high lane when j / 2 is odd)
-  if (x0 == 0 || x0 + 18 > W) {
+  if (__any_sync(0xFFFFFFFFu, x0 == 0 || x0 + 18 > W)) {
     if (x0 == 0) {  // window columns 0 and 1 (low lanes of words 0 and 1) <- window column 2
       const uint32_t yf = yp[0] >> 16;
       yp[0] = (yp[0] & 0xFFFF0000u) | yf;
@@ -165,63 +165,60 @@ __device__ __forceinline__ uint4 luma16(const uint8_t *row, int x0) {
   return make_uint4(d[0], d[1], d[2], d[3]);
 }
 
-// Vertical binomial [1 4 6 4 1] as four cascaded [1 1] sums over the stream of
-// luminance rows.  The 20 columns are held as 10 words of two 16-bit lanes: lo[q] =
-// columns (4q, 4q+2), hi[q] = (4q+1, 4q+3) of the window x0-2 .. x0+17.  After a row n
-// is fed, p0 = Y(n), p1 = Y(n-1)+Y(n), p2 and p3 the next sums; feeding row n+1 returns
-// sum_i C(4,i) Y(n-3+i), the vertical binomial centred on row n-1.  All sums stay below
-// 16 * 255, so the lanes never carry into each other.
+// Horizontal binomial [1 4 6 4 1] of one row's luminance, before rounding: from the 10
+// pair words of the window x0-2 .. x0+17 (luma20's layout) to the 16 own columns as 8 pair
+// words, h[2k] = columns (4k, 4k+2), h[2k+1] = (4k+1, 4k+3).  Sums stay below 16 * 255.
+__device__ __forceinline__ void binom_h(const uint32_t (&Y)[10], uint32_t (&h)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t E0 = Y[2 * k], O0 = Y[2 * k + 1], E1 = Y[2 * k + 2], O1 = Y[2 * k + 3];
+    const uint32_t se = __byte_perm(E0, E1, 0x5432);  // window columns (4k+2, 4k+4)
+    const uint32_t so = __byte_perm(O0, O1, 0x5432);  // (4k+3, 4k+5)
+    h[2 * k] = E0 + E1 + 4u * (O0 + so) + 6u * se;      // own columns 4k, 4k+2
+    h[2 * k + 1] = O0 + O1 + 4u * (se + E1) + 6u * so;  // own columns 4k+1, 4k+3
+  }
+}
+
+// Vertical binomial [1 4 6 4 1] of the row sums as four cascaded [1 1] sums over the
+// stream of rows, on the 8 pair words of binom_h.  After row n is fed, p0 = h(n),
+// p1 = h(n-1) + h(n), p2 and p3 the next sums; feeding row n+1 returns
+// sum_i C(4,i) h(n-3+i), the full 5x5 sum centred on row n-1 (at most 256 * 255, so the
+// lanes never carry into each other).  The state is updated in place: the new p3 is the
+// sum minus the old p3, each lower level the level above minus its old value.
 struct VCascade {
-  uint32_t p0[10], p1[10], p2[10], p3[10];
+  uint32_t p0[8], p1[8], p2[8], p3[8];
 
   __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int i = 0; i < 10; ++i) p0[i] = p1[i] = p2[i] = p3[i] = 0u;
+    for (int i = 0; i < 8; ++i) p0[i] = p1[i] = p2[i] = p3[i] = 0u;
   }
-  // feeds one row (16-bit lane pairs); V receives the vertical sums (valid from the
-  // fifth row on)
-  __device__ __forceinline__ void feed(const uint32_t (&y)[10], uint32_t (&V)[10]) {
+  __device__ __forceinline__ void feed(const uint32_t (&h)[8], uint32_t (&V)[8]) {
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-      const uint32_t a1 = p0[i] + y[i];
-      const uint32_t a2 = p1[i] + a1;
-      const uint32_t a3 = p2[i] + a2;
-      V[i] = p3[i] + a3;
-      p0[i] = y[i];
-      p1[i] = a1;
-      p2[i] = a2;
-      p3[i] = a3;
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t v = p3[i] + p2[i] + p1[i] + p0[i] + h[i];
+      p3[i] = v - p3[i];
+      p2[i] = p3[i] - p2[i];
+      p1[i] = p2[i] - p1[i];
+      p0[i] = p1[i] - p0[i];
+      V[i] = v;
     }
   }
   // feeds the newest row again (the image's last row repeated below the image)
-  __device__ __forceinline__ void feed_repeat(uint32_t (&V)[10]) {
+  __device__ __forceinline__ void feed_repeat(uint32_t (&V)[8]) {
+    uint32_t h[8];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-      const uint32_t a1 = p0[i] + p0[i];
-      const uint32_t a2 = p1[i] + a1;
-      const uint32_t a3 = p2[i] + a2;
-      V[i] = p3[i] + a3;
-      p1[i] = a1;
-      p2[i] = a2;
-      p3[i] = a3;
-    }
+    for (int i = 0; i < 8; ++i) h[i] = p0[i];
+    feed(h, V);
   }
 };
 
-// Horizontal binomial of the vertical sums and rounding: D = (sum + 128) >> 8 for the 16
-// own columns (window columns 2..17), packed 4 per word.  Both lanes of a sum word stay
-// below 65536 after the rounding offset, so byte 1 of each lane is its rounded result.
-__device__ __forceinline__ uint4 binom_h(const uint32_t (&V)[10]) {
+// The depth of the 16 own columns from the 5x5 sums: D = (sum + 128) >> 8, packed 4 per
+// word.  Both lanes of a sum word stay below 65536 after the rounding offset, so byte 1 of
+// each lane is its rounded result.
+__device__ __forceinline__ uint4 round_depth(const uint32_t (&V)[8]) {
   uint32_t d[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t E0 = V[2 * k], O0 = V[2 * k + 1], E1 = V[2 * k + 2], O1 = V[2 * k + 3];
-    const uint32_t se = __byte_perm(E0, E1, 0x5432);  // (V[4k+2], V[4k+4])
-    const uint32_t so = __byte_perm(O0, O1, 0x5432);  // (V[4k+3], V[4k+5])
-    const uint32_t pe = E0 + E1 + 0x00800080u + 4u * (O0 + so) + 6u * se;  // columns 4k, 4k+2
-    const uint32_t po = O0 + O1 + 0x00800080u + 4u * (se + E1) + 6u * so;  // columns 4k+1, 4k+3
-    d[k] = __byte_perm(pe, po, 0x7351);
-  }
+  for (int k = 0; k < 4; ++k) d[k] = __byte_perm(V[2 * k] + 0x00800080u, V[2 * k + 1] + 0x00800080u, 0x7351);
   return make_uint4(d[0], d[1], d[2], d[3]);
 }
 
@@ -287,6 +284,39 @@ __device__ __forceinline__ void store16(uint8_t *p, uint4 v, int npx) {
   }
 }
 
+// Bit j of m set for every entry of k that is not kEmpty: a compare and a predicated OR
+// per entry.
+__device__ __forceinline__ uint32_t filled_mask(const uint32_t (&k)[16]) {
+  uint32_t m = 0u;
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, -1;\n\t@p or.b32 %0, %0, %2;\n\t}" : "+r"(m) : "r"(k[j]), "r"(1u << j));
+  return m;
+}
+
+// Left to right: every entry whose bit of m is clear takes the last entry with its bit set
+// (c: the entry carried in).
+__device__ __forceinline__ void carry_right(uint32_t (&k)[16], uint32_t m, uint32_t c) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.u32 p, t, 0;\n\t"
+        "selp.b32 %1, %0, %1, p;\n\tmov.b32 %0, %1;\n\t}"
+        : "+r"(k[j]), "+r"(c) : "r"(m), "r"(1u << j));
+  }
+}
+
+// Right to left: c carries the last entry with its bit set (c: the entry carried in), and
+// an entry whose bit is clear takes c where c is strictly farther (c > (k | 0xFFFFFF)).
+__device__ __forceinline__ void carry_left_farther(uint32_t (&k)[16], uint32_t m, uint32_t c) {
+#pragma unroll
+  for (int j = 15; j >= 0; --j) {
+    asm("{\n\t.reg .pred p, q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.u32 p, t, 0;\n\t"
+        "selp.b32 %1, %0, %1, p;\n\tor.b32 t, %0, 0xFFFFFF;\n\tsetp.gt.u32 q, %1, t;\n\t"
+        "selp.b32 %0, %1, %0, q;\n\t}"
+        : "+r"(k[j]), "+r"(c) : "r"(m), "r"(1u << j));
+  }
+}
+
 // A red.shared.min at a + OFF when pred holds (no branch).
 template <int OFF>
 __device__ __forceinline__ void reds_min_at_if(uint32_t a, uint32_t v, bool pred) {
@@ -347,7 +377,7 @@ struct Shm {
   uint64_t *sdone;  // every warp has published its summary and cleared its targets (C)
   uint2 *lut;       // per 255 - depth: byte offsets of the left / right targets
   int32_t *lut_n;   // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
-  uint8_t *wsum;    // [parity][warp][view] uint4 {has, first entry, last entry, 0}
+  uint8_t *wsum;    // [parity][view][warp] uint4 {has, first entry, last entry, 0}
   uint8_t *ring, *drow;
   uint32_t zb;      // shared address of the z-buffer region
   int nb, srow, zlen, zstride, zguard;
@@ -390,18 +420,23 @@ __device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, co
 
 // Every thread's wait on an mbarrier phase, the outcome agreed within the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns) {
-  const bool ok = mbar_wait_bounded(bar, parity, timeout_ns);
-  return __all_sync(kAll, ok);
+  if (__all_sync(kAll, mbar_try_wait(bar, parity))) return true;
+  const unsigned long long t0 = __shfl_sync(kAll, global_ns(), 0);
+  while (true) {
+    if (__all_sync(kAll, mbar_try_wait(bar, parity))) return true;
+    if (__shfl_sync(kAll, global_ns(), 0) - t0 > timeout_ns) return false;
+  }
 }
 
 // Rows [ys, ye) of one image, every stage of the pipeline (see the file comment).  All
 // threads of the CTA call it together.  kbase counts the ring loads this CTA issued
-// before (the slot and mbarrier phase of a load follow from it), bph / sph the completed
-// phases of the two per-row mbarriers; all three are advanced here.  Returns false when a
-// bounded wait gave up (the status word is set and the copies in flight have landed).
+// before (the slot and mbarrier phase of a load follow from it), nrows the rows the CTA
+// processed before (each per-row mbarrier completes one phase per row); both are advanced
+// here.  Returns false when a bounded wait gave up (the status word is set and the copies
+// in flight have landed).
 template <int DS, bool FWD>
 __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
-                                         uint32_t &bph, uint32_t &sph, int *status,
+                                         uint32_t &nrows, int *status,
                                          unsigned long long timeout_ns) {
   constexpr bool binom = DS == DS_BINOM5;
   const int tid = threadIdx.x, nc = blockDim.x, W = a.W, H = a.H, nb = m.nb;
@@ -421,7 +456,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   // all warps (every warp has scattered it: the bdone mbarrier, or a CTA barrier).
   int issued = 0;
   const int lw = 32 * (nwarps >> 1);  // first thread of the loading warp
-  const bool loader = (tid >> 5) == (nwarps >> 1);
+  const bool loader = __shfl_sync(kAll, (tid >> 5) == (nwarps >> 1), 0);
   auto issue_loads = [&](int upto) {
     upto = min(upto, nload);
     if (tid == lw && issued == 0 && a.load_mode != LM_BULK) prefetch_tensormap(a.tmap);
@@ -469,6 +504,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   const int npx = max(0, min(kChunk, W - x0));
   const bool active = npx > 0;
   const bool own_chunk = tid < a.nch;            // the thread's chunk exists (active or not)
+  // the warp's 32 chunks are all whole (every warp of a row but possibly the last):
+  // warp-uniform fast paths for its depth row, clears and stores
+  const bool wfull = __all_sync(kAll, npx == kChunk);
+  const bool wfast = wfull && a.fast_store;
   const int x0c = min(x0, (a.nch - 1) * kChunk);  // clamped: loads stay inside the buffers
   const int warp_lo = (tid & ~31) * kChunk;
   const int warp_hi = min(W, warp_lo + 32 * kChunk);
@@ -508,9 +547,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 #pragma unroll 1
     for (int i = -2; i <= 1; ++i) {
       const int r = min(max(ys + i, 0), H - 1);
-      uint32_t yq[10], V[10];
+      uint32_t yq[10], hq[8], V[8];
       luma20(slot(r), x0c, W, yq);
-      vc.feed(yq, V);
+      binom_h(yq, hq);
+      vc.feed(hq, V);
     }
   }
   // the cleared z-buffers (and, with the binomial, the rows above the band) are done with
@@ -525,15 +565,16 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     if (binom) {
       const int r2 = y + 2;
       if (r2 < lb) wait_row(r2);
-      uint32_t V[10];
+      uint32_t V[8];
       if (r2 < H) {
-        uint32_t yq[10];
+        uint32_t yq[10], hq[8];
         luma20(slot(r2), x0c, W, yq);
-        vc.feed(yq, V);
+        binom_h(yq, hq);
+        vc.feed(hq, V);
       } else {
         vc.feed_repeat(V);  // rows below the image repeat row H-1
       }
-      d = binom_h(V);
+      d = round_depth(V);
     } else if (DS == DS_LUMA) {
       wait_row(y);
       d = luma16(slot(y), x0c);
@@ -552,7 +593,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       }
     }
     if (want_depth && active) store16(a.out[O_DEPTH] + static_cast<int64_t>(y) * a.depth_pitch + x0, d, npx);
-    if (FWD && own_chunk) *reinterpret_cast<uint4 *>(m.drow + x0) = make_uint4(~d.x, ~d.y, ~d.z, ~d.w);
+    if (FWD && (wfull || own_chunk)) *reinterpret_cast<uint4 *>(m.drow + x0) = make_uint4(~d.x, ~d.y, ~d.z, ~d.w);
     return d;
   };
 
@@ -605,24 +646,67 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       }
     }
   };
-  auto arrive_b = [&]() {
-    __syncwarp();
-    if (lane == 0) mbar_arrive(m.bdone);
-  };
+  // the parity of row y's phase of the per-row mbarriers
+  auto par = [&](int y) { return (nrows + static_cast<uint32_t>(y - ys)) & 1u; };
+  auto arrive_b = [&](int) { mbar_arrive(m.bdone); };
 
   // ---- C: row y's targets: winners, hole fill, formatting, stores
-  auto wsum_at = [&](int p, int w, int v) { return smem_addr(m.wsum) + 16u * static_cast<uint32_t>((p * nwarps + w) * 2 + v); };
+  auto wsum_at = [&](int p, int v, int w) { return smem_addr(m.wsum) + 16u * static_cast<uint32_t>((p * 2 + v) * nwarps + w); };
+
+  // this lane's clears: 16 bytes at warp_lo + 4 * lane + 128 q targets, q = 0..3
+  const uint32_t clr_off = 4u * static_cast<uint32_t>(warp_lo + 4 * lane);
   auto phase_c = [&](int y, uint4 d) {
     // every warp has scattered row y: its targets are final and its ring slot is free
-    if (!warp_wait(m.bdone, (bph + static_cast<uint32_t>(y - ys)) & 1u, timeout_ns)) timed_out = true;
+    if (!warp_wait(m.bdone, par(y), timeout_ns)) timed_out = true;
     if (loader) issue_loads((y - la) + 1 + nb);
     const uint8_t *grow = a.in + static_cast<int64_t>(y) * a.in_pitch;
     const int p = y & 1;
+    // Formatting and stores of one view's 16 targets: the view itself, its half of the
+    // side-by-side frame and, after the right view, the anaglyph (red from the left view,
+    // green and blue from the right: in the packed words, the bytes at offsets 0 mod 3).
+    const int64_t ro = static_cast<int64_t>(y) * a.out_pitch;
+    const bool fast = wfast || (a.fast_store && npx == kChunk);
+    uint32_t wl[12];
+    auto emit_view = [&](int v, const uint32_t (&kv)[16]) {
+      if (!wfull && !active) return;
+      uint32_t w[12];
+      pack16(kv, w);
+      if (v == 0) {
+        if (want_l) store48(a.out[O_LEFT] + ro + 3 * x0, w, npx, fast);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) wl[i] = w[i];
+      } else {
+        if (want_r) store48(a.out[O_RIGHT] + ro + 3 * x0, w, npx, fast);
+        if (want_ana) {
+          uint32_t wa[12];
+#pragma unroll
+          for (int i = 0; i < 12; ++i) {
+            const uint32_t M = i % 3 == 0 ? 0xFF0000FFu : i % 3 == 1 ? 0x00FF0000u : 0x0000FF00u;
+            wa[i] = (wl[i] & M) | (w[i] & ~M);
+          }
+          store48(a.out[O_ANA] + ro + 3 * x0, wa, npx, fast);
+        }
+      }
+      if (want_hsbs) {
+        uint32_t c8[8], h6[6];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) c8[j] = avg_up(kv[2 * j], kv[2 * j + 1]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          h6[3 * q] = __byte_perm(c8[4 * q], c8[4 * q + 1], 0x4210);
+          h6[3 * q + 1] = __byte_perm(c8[4 * q + 1], c8[4 * q + 2], 0x5421);
+          h6[3 * q + 2] = __byte_perm(c8[4 * q + 2], c8[4 * q + 3], 0x6542);
+        }
+        // W is even, so chunks hold whole pairs; the left view fills the left half
+        store24(a.out[O_HSBS] + ro + 3 * ((v == 0 ? 0 : W / 2) + x0 / 2), h6, npx / 2);
+      }
+    };
     uint32_t k[2][16];
     uint32_t hole[2] = {0u, 0u};
     if (FWD) {
       const uint32_t rowmask = npx >= kChunk ? 0xFFFFu : ((1u << npx) - 1u);
       uint32_t mm[2], fe[2], cl[2], cr[2], lanes[2];
+
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
         const uint32_t za = zrow(p, v) + 4u * static_cast<uint32_t>(x0c);
@@ -631,10 +715,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
           const uint4 u = lds_u32x4(za + 16u * q);
           k[v][4 * q] = u.x; k[v][4 * q + 1] = u.y; k[v][4 * q + 2] = u.z; k[v][4 * q + 3] = u.w;
         }
-        uint32_t mk = 0u;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) mk |= (k[v][j] != kEmpty ? 1u : 0u) << j;
-        mk &= rowmask;
+        const uint32_t mk = filled_mask(k[v]) & rowmask;
         // the chunk's first and last filled entries, for the neighbouring lanes
         const int fj = __ffs(mk) - 1, lj = 31 - __clz(mk);
         fe[v] = lds_u32(za + 4u * static_cast<uint32_t>(fj & 15));
@@ -645,7 +726,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         cr[v] = __shfl_sync(kAll, fe[v], (__ffs(upper) - 1) & 31);
         const uint32_t wf = __shfl_sync(kAll, fe[v], (__ffs(ln) - 1) & 31);
         const uint32_t wl = __shfl_sync(kAll, le, (31 - __clz(ln)) & 31);
-        if (lane == 0) sts_u32x4(wsum_at(p, warp, v), make_uint4(ln != 0u ? 1u : 0u, wf, wl, 0u));
+        sts_u32x4(wsum_at(p, v, warp), make_uint4(ln != 0u ? 1u : 0u, wf, wl, 0u));  // (same value, every lane)
         mm[v] = mk;
         lanes[v] = ln;
       }
@@ -654,16 +735,22 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       // summary is published and its targets are clear
       __syncwarp();
       const uint4 e4 = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+      const uint32_t c0 = zrow(p, 0) + clr_off, c1 = zrow(p, 1) + clr_off;
+      if (wfull) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int t = warp_lo + 4 * (32 * q + lane);
-        if (t < m.zlen) {
-          sts_u32x4(zrow(p, 0) + 4u * t, e4);
-          sts_u32x4(zrow(p, 1) + 4u * t, e4);
+        for (int q = 0; q < 4; ++q) {
+          sts_u32x4(c0 + 512u * q, e4);
+          sts_u32x4(c1 + 512u * q, e4);
         }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (warp_lo + 4 * (32 * q + lane) < m.zlen) {
+            sts_u32x4(c0 + 512u * q, e4);
+            sts_u32x4(c1 + 512u * q, e4);
+          }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(m.sdone);
+      mbar_arrive(m.sdone);
       // entries from outside the warp, for lanes whose leading (trailing) holes have no
       // filled target below (above) them in the warp: the nearest warp's last (first)
       // filled entry, from the summaries
@@ -676,25 +763,19 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       uint32_t wle[2] = {0u, 0u}, wre[2] = {0u, 0u};
       bool wlh[2] = {false, false}, wrh[2] = {false, false};
       if (__any_sync(kAll, need)) {
-        if (!warp_wait(m.sdone, (sph + static_cast<uint32_t>(y - ys)) & 1u, timeout_ns)) timed_out = true;
+        if (!warp_wait(m.sdone, par(y), timeout_ns)) timed_out = true;
+        // lane w reads warp w's summary; the nearest warp below / above with a filled target
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
-          for (int w = warp - 1; w >= 0; --w) {
-            const uint4 s = lds_u32x4(wsum_at(p, w, v));
-            if (s.x) {
-              wle[v] = s.z;
-              wlh[v] = true;
-              break;
-            }
-          }
-          for (int w = warp + 1; w < nwarps; ++w) {
-            const uint4 s = lds_u32x4(wsum_at(p, w, v));
-            if (s.x) {
-              wre[v] = s.y;
-              wrh[v] = true;
-              break;
-            }
-          }
+          const uint4 sm = lds_u32x4(wsum_at(p, v, lane < nwarps ? lane : 0));
+          const uint32_t has = __ballot_sync(kAll, lane < nwarps && sm.x != 0u);
+          const uint32_t below = has & ((1u << warp) - 1u), above = has & ~((2u << warp) - 1u);
+          const uint32_t el = __shfl_sync(kAll, sm.z, (31 - __clz(below)) & 31);
+          const uint32_t er = __shfl_sync(kAll, sm.y, (__ffs(above) - 1) & 31);
+          wlh[v] = below != 0u;
+          wrh[v] = above != 0u;
+          wle[v] = below ? el : 0u;
+          wre[v] = above ? er : 0u;
         }
       }
       // Hole fill: a hole shows the winner of the nearest filled target on its farther
@@ -712,28 +793,18 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         const uint32_t lower = lanes[v] & ltm, upper = lanes[v] & gtm, mk = mm[v];
         const uint32_t rin = upper ? cr[v] : wre[v];
         const uint32_t lin = lower ? cl[v] : (wlh[v] ? wle[v] : (mk ? fe[v] : rin));
-        uint32_t c = lin;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          c = ((mk >> j) & 1u) ? k[v][j] : c;
-          k[v][j] = c;
-        }
-        c = rin;
-#pragma unroll
-        for (int j = 15; j >= 0; --j) {
-          c = ((mk >> j) & 1u) ? k[v][j] : c;
-          k[v][j] = c > (k[v][j] | 0xFFFFFFu) ? c : k[v][j];
-        }
+        carry_right(k[v], mk, lin);
+        carry_left_farther(k[v], mk, rin);
         hole[v] = ~mk & rowmask;
         if (lanes[v] == 0u && !wlh[v] && !wrh[v]) {  // (warp-uniform)
 #pragma unroll
           for (int j = 0; j < 16; ++j) k[v][j] = active ? rgb_at_global(grow, min(x0 + j, W - 1)) : 0u;
         }
+        emit_view(v, k[v]);
       }
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
-      __syncwarp();
-      if (lane == 0) mbar_arrive(m.sdone);
+      mbar_arrive(m.sdone);
       const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
       for (int i = 0; i < kChunk; ++i) {
@@ -745,6 +816,8 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
         k[0][i] = active ? rgb_at_global(grow, sl) : 0u;
         k[1][i] = active ? rgb_at_global(grow, sr) : 0u;
       }
+      emit_view(0, k[0]);
+      emit_view(1, k[1]);
     }
     if (active && want_holes) {
       // one byte per target: bit 0 a hole of the left view, bit 1 of the right view
@@ -756,67 +829,24 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       hv.w = spread4(hole[0] >> 12) | (spread4(hole[1] >> 12) << 1);
       store16(a.out[O_HOLES] + static_cast<int64_t>(y) * a.depth_pitch + x0, hv, npx);
     }
-    if (active) {
-      const int64_t ro = static_cast<int64_t>(y) * a.out_pitch + 3 * x0;
-      const bool fast = a.fast_store && npx == kChunk;
-      uint32_t wl[12], wr[12];
-      pack16(k[0], wl);
-      pack16(k[1], wr);
-      if (want_l) store48(a.out[O_LEFT] + ro, wl, npx, fast);
-      if (want_r) store48(a.out[O_RIGHT] + ro, wr, npx, fast);
-      if (want_ana) {
-        // red from the left view, green and blue from the right: in the packed words the
-        // red bytes are the bytes at offsets 0 mod 3
-        uint32_t wa[12];
-#pragma unroll
-        for (int i = 0; i < 12; ++i) {
-          const uint32_t M = i % 3 == 0 ? 0xFF0000FFu : i % 3 == 1 ? 0x00FF0000u : 0x0000FF00u;
-          wa[i] = (wl[i] & M) | (wr[i] & ~M);
-        }
-        store48(a.out[O_ANA] + ro, wa, npx, fast);
-      }
-      if (want_hsbs) {
-        uint32_t cl8[8], cr8[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          cl8[j] = avg_up(k[0][2 * j], k[0][2 * j + 1]);
-          cr8[j] = avg_up(k[1][2 * j], k[1][2 * j + 1]);
-        }
-        uint32_t hl[6], hr[6];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          hl[3 * q] = __byte_perm(cl8[4 * q], cl8[4 * q + 1], 0x4210);
-          hl[3 * q + 1] = __byte_perm(cl8[4 * q + 1], cl8[4 * q + 2], 0x5421);
-          hl[3 * q + 2] = __byte_perm(cl8[4 * q + 2], cl8[4 * q + 3], 0x6542);
-          hr[3 * q] = __byte_perm(cr8[4 * q], cr8[4 * q + 1], 0x4210);
-          hr[3 * q + 1] = __byte_perm(cr8[4 * q + 1], cr8[4 * q + 2], 0x5421);
-          hr[3 * q + 2] = __byte_perm(cr8[4 * q + 2], cr8[4 * q + 3], 0x6542);
-        }
-        const int np = npx / 2;  // W is even, so chunks hold whole pairs
-        const int64_t rh = static_cast<int64_t>(y) * a.out_pitch;
-        store24(a.out[O_HSBS] + rh + 3 * (x0 / 2), hl, np);
-        store24(a.out[O_HSBS] + rh + 3 * (W / 2 + x0 / 2), hr, np);
-      }
-    }
   };
 
   uint4 dcur = make_uint4(0u, 0u, 0u, 0u);
   if (!aborted) {
     dcur = phase_a(ys);
     phase_b(ys);
-    arrive_b();
+    arrive_b(ys);
   }
   for (int y = ys; y < ye && !aborted && !timed_out; ++y) {
     // the loader refills the slot of row y as soon as every warp has scattered it
-    if (loader && __any_sync(kAll, mbar_test(m.bdone, (bph + static_cast<uint32_t>(y - ys)) & 1u)))
-      issue_loads((y - la) + 1 + nb);
+    if (loader && __any_sync(kAll, mbar_test(m.bdone, par(y)))) issue_loads((y - la) + 1 + nb);
     const bool more = y + 1 < ye;
     uint4 dnext = make_uint4(0u, 0u, 0u, 0u);
     if (more) dnext = phase_a(y + 1);
     phase_c(y, dcur);
     if (more) {
       phase_b(y + 1);
-      arrive_b();
+      arrive_b(y + 1);
     }
     dcur = dnext;
   }
@@ -835,16 +865,15 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     return false;
   }
   kbase = k0 + static_cast<uint32_t>(nload);
-  bph += static_cast<uint32_t>(ye - ys);
-  sph += static_cast<uint32_t>(ye - ys);
+  nrows += static_cast<uint32_t>(ye - ys);
   return true;
 }
 
 __device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < nb; ++i) mbar_init(&m.full[i], 1);
-    mbar_init(m.bdone, blockDim.x / 32);
-    mbar_init(m.sdone, blockDim.x / 32);
+    mbar_init(m.bdone, blockDim.x);
+    mbar_init(m.sdone, blockDim.x);
     fence_mbar_init();
   }
 }
@@ -883,8 +912,8 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
     j.W = a.W; j.H = a.H; j.nch = a.nch; j.row_bytes = a.row_bytes; j.load_mode = a.load_mode;
     j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
     j.outputs = a.outputs; j.l2_prefetch = a.l2_prefetch; j.fast_store = a.fast_store;
-    uint32_t kbase = 0, bph = 0, sph = 0;
-    run_band<DS, FWD>(j, m, ys, ye, kbase, bph, sph, a.status, a.timeout_ns);
+    uint32_t kbase = 0, nrows = 0;
+    run_band<DS, FWD>(j, m, ys, ye, kbase, nrows, a.status, a.timeout_ns);
   }
   if (a.overlap) griddep_wait();
 }
@@ -903,7 +932,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
   const Shm m0 = carve(smem, b.nb, b.srow, b.nch_max, nwarps, b.zguard);
   int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, nwarps, b.zguard).flags);
   init_barriers(m0, b.nb);
-  uint32_t kbase = 0, bph = 0, sph = 0;
+  uint32_t kbase = 0, nrows = 0;
   while (true) {
     __syncthreads();  // the previous unit is done with the ring, tables and unit_s
     if (threadIdx.x == 0) *unit_s = atomicAdd(b.counter, 1);
@@ -936,12 +965,12 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     __syncthreads();
     bool ok;
     switch (dsc.depth_src * 2 + (fwd ? 0 : 1)) {
-      case DS_BINOM5 * 2: ok = run_band<DS_BINOM5, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
-      case DS_BINOM5 * 2 + 1: ok = run_band<DS_BINOM5, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
-      case DS_LUMA * 2: ok = run_band<DS_LUMA, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
-      case DS_LUMA * 2 + 1: ok = run_band<DS_LUMA, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
-      case DS_GLOBAL * 2: ok = run_band<DS_GLOBAL, true>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
-      default: ok = run_band<DS_GLOBAL, false>(j, m, un.y, un.z, kbase, bph, sph, b.status, b.timeout_ns); break;
+      case DS_BINOM5 * 2: ok = run_band<DS_BINOM5, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
+      case DS_BINOM5 * 2 + 1: ok = run_band<DS_BINOM5, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
+      case DS_LUMA * 2: ok = run_band<DS_LUMA, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
+      case DS_LUMA * 2 + 1: ok = run_band<DS_LUMA, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
+      case DS_GLOBAL * 2: ok = run_band<DS_GLOBAL, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
+      default: ok = run_band<DS_GLOBAL, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
     }
     if (!ok) break;
   }

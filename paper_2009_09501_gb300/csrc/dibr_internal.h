@@ -93,9 +93,9 @@ struct BandArgs {
 // Shared-memory layout of the band kernel (bytes from the dynamic smem base).
 //   bar   ring-slot mbarriers full[kMaxRing]
 //   flags +0: the batch's current work unit; +8, +16: the per-row mbarriers (every warp
-//         has scattered the row / has read and cleared its targets of the row)
+//         has scattered the row / has published its summary and cleared its targets)
 //   lut   uint2 per value of 255 - depth: byte offsets of the left / right target
-//   wsum  per row parity, warp and view: {has a filled target, first, last filled entry}
+//   wsum  per row parity, view and warp: {has a filled target, first, last filled entry}
 //   ring  input rows;  drow  255 - depth of the current row, one byte per column
 //   zb    z-buffers, [parity][view] rows of zlen targets separated by zguard guard targets
 //         (targets a shift moves outside the row land in a guard and are never read);
@@ -112,7 +112,7 @@ __host__ __device__ inline BandSmem band_smem_layout(int nb, int srow, int nch, 
   s.flags = 8 * kMaxRing;
   s.lut = s.flags + 64;
   s.wsum = s.lut + 2048;
-  s.ring = round_up(s.wsum + 2 * nwarps * 2 * 16, 128);
+  s.ring = round_up(s.wsum + 2 * 2 * nwarps * 16, 128);
   s.drow = round_up(s.ring + nb * srow, 16);
   s.zb = round_up(s.drow + nch * kChunk, 16);
   const int zlen = nch * kChunk;  // a multiple of 16 targets: rows stay 16-byte aligned
