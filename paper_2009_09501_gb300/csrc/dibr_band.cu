@@ -25,12 +25,14 @@
 //      across chunks come from the neighbouring lanes by shuffle, across warps from a
 //      per-warp summary in shared memory), formats and stores the outputs, and clears
 //      its warp's targets for the row two rows later.
-// Rows interleave as A(y+1), C(y), B(y+1).  There is no CTA-wide barrier per row: C of a
-// row waits on an mbarrier every warp arrives on after B of that row, and a warp that
-// needs an entry from outside its own targets waits on a second one every warp arrives
-// on once it has published its summary and cleared its targets.  Every wait is bounded
-// (%globaltimer); a wait that gives up sets a bit of the status word and the CTA unwinds
-// after letting its own copies land.
+// Rows interleave as A(y+1), B(y+1), C(y).  There is no CTA-wide barrier per row: C of a
+// row waits on an mbarrier every warp arrives on after B of that row (a row earlier), B of
+// a row waits on one every warp arrives on once it has published its summary of the row
+// two rows before and cleared its targets there (the same z-buffer), and a warp that needs
+// an entry from outside its own targets waits on that second one for its own row.  The
+// barriers come in pairs used by alternate rows.  Every wait is bounded (%globaltimer); a
+// wait that gives up sets a bit of the status word and the CTA unwinds after letting its
+// own copies land.
 #include <atomic>
 
 #include "dibr.h"
@@ -373,8 +375,8 @@ struct Job {
 // Shared-memory regions of one CTA.
 struct Shm {
   uint64_t *full;   // ring-slot mbarriers
-  uint64_t *bdone;  // every warp has scattered the row (B)
-  uint64_t *sdone;  // every warp has published its summary and cleared its targets (C)
+  uint64_t *bdone;  // [2] every warp has scattered the row (B)
+  uint64_t *sdone;  // [2] every warp has published its summary and cleared its targets (C)
   uint2 *lut;       // per 255 - depth: byte offsets of the left / right targets
   int32_t *lut_n;   // Fig. 3 gather: 510 * s_L(d) (in the z-buffer region)
   uint8_t *wsum;    // [parity][view][warp] uint4 {has, first entry, last entry, 0}
@@ -388,7 +390,7 @@ __device__ __forceinline__ Shm carve(uint8_t *smem, int nb, int srow, int nch, i
   Shm m;
   m.full = reinterpret_cast<uint64_t *>(smem + L.bar);
   m.bdone = reinterpret_cast<uint64_t *>(smem + L.flags + 8);
-  m.sdone = reinterpret_cast<uint64_t *>(smem + L.flags + 16);
+  m.sdone = reinterpret_cast<uint64_t *>(smem + L.flags + 24);
   m.lut = reinterpret_cast<uint2 *>(smem + L.lut);
   m.wsum = smem + L.wsum;
   m.ring = smem + L.ring;
@@ -541,12 +543,11 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   VCascade vc;
   vc.clear();
   if (binom) {
-    // rows clamp(ys-2) .. clamp(ys+1) into the cascade
-    const int pend = min(ys + 1, lb - 1);
-    for (int r = la; r <= pend; ++r) wait_row(r);
+    // rows clamp(ys-2) .. clamp(ys+1) into the cascade, each as soon as it has landed
 #pragma unroll 1
     for (int i = -2; i <= 1; ++i) {
       const int r = min(max(ys + i, 0), H - 1);
+      if (r >= la && r < lb && (i == -2 || r != min(max(ys + i - 1, 0), H - 1))) wait_row(r);
       uint32_t yq[10], hq[8], V[8];
       luma20(slot(r), x0c, W, yq);
       binom_h(yq, hq);
@@ -558,6 +559,14 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   if (!aborted && loader) issue_loads((ys - la) + nb);
 
   const uint32_t ltm = lanemask_lt(), gtm = lanemask_gt();
+
+  // The per-row mbarriers come in pairs: the CTA's r-th row (r = nrows + y - ys) uses
+  // barrier r & 1 of a pair, phase r >> 1, so that phases of rows two apart never meet.
+  auto rix = [&](int y) { return nrows + static_cast<uint32_t>(y - ys); };
+  auto bbar = [&](int y) { return m.bdone + (rix(y) & 1u); };
+  auto sbar = [&](int y) { return m.sdone + (rix(y) & 1u); };
+  auto par = [&](int y) { return (rix(y) >> 1) & 1u; };
+  auto arrive_b = [&](int y) { mbar_arrive(bbar(y)); };
 
   // ---- A: the depth of row y (registers, 4 per word), 255 - depth into the depth row
   auto phase_a = [&](int y) -> uint4 {
@@ -602,6 +611,9 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   // (shifts vary slowly); all shared loads of four steps are issued before their atomics
   auto phase_b = [&](int y) {
     if (!FWD) return;
+    // every warp has cleared its targets of row y - 2, the previous user of this z-buffer
+    // (the band's first two rows use the buffers cleared before the band)
+    if (y >= ys + 2 && !warp_wait(m.sdone + (rix(y - 2) & 1u), par(y - 2), timeout_ns)) timed_out = true;
     const int xb = warp_lo + lane;
     const uint32_t ob = 3u * static_cast<uint32_t>(xb);
     const uint32_t cws = smem_addr(slot(y)) + (ob & ~3u);  // the lane's colours: +96 bytes per step
@@ -646,9 +658,6 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       }
     }
   };
-  // the parity of row y's phase of the per-row mbarriers
-  auto par = [&](int y) { return (nrows + static_cast<uint32_t>(y - ys)) & 1u; };
-  auto arrive_b = [&](int) { mbar_arrive(m.bdone); };
 
   // ---- C: row y's targets: winners, hole fill, formatting, stores
   auto wsum_at = [&](int p, int v, int w) { return smem_addr(m.wsum) + 16u * static_cast<uint32_t>((p * 2 + v) * nwarps + w); };
@@ -657,7 +666,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   const uint32_t clr_off = 4u * static_cast<uint32_t>(warp_lo + 4 * lane);
   auto phase_c = [&](int y, uint4 d) {
     // every warp has scattered row y: its targets are final and its ring slot is free
-    if (!warp_wait(m.bdone, par(y), timeout_ns)) timed_out = true;
+    if (!warp_wait(bbar(y), par(y), timeout_ns)) timed_out = true;
     if (loader) issue_loads((y - la) + 1 + nb);
     const uint8_t *grow = a.in + static_cast<int64_t>(y) * a.in_pitch;
     const int p = y & 1;
@@ -750,7 +759,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
             sts_u32x4(c1 + 512u * q, e4);
           }
       }
-      mbar_arrive(m.sdone);
+      mbar_arrive(sbar(y));
       // entries from outside the warp, for lanes whose leading (trailing) holes have no
       // filled target below (above) them in the warp: the nearest warp's last (first)
       // filled entry, from the summaries
@@ -763,7 +772,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       uint32_t wle[2] = {0u, 0u}, wre[2] = {0u, 0u};
       bool wlh[2] = {false, false}, wrh[2] = {false, false};
       if (__any_sync(kAll, need)) {
-        if (!warp_wait(m.sdone, par(y), timeout_ns)) timed_out = true;
+        if (!warp_wait(sbar(y), par(y), timeout_ns)) timed_out = true;
         // lane w reads warp w's summary; the nearest warp below / above with a filled target
 #pragma unroll
         for (int v = 0; v < 2; ++v) {
@@ -804,7 +813,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       }
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
-      mbar_arrive(m.sdone);
+      mbar_arrive(sbar(y));
       const uint32_t dw[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
       for (int i = 0; i < kChunk; ++i) {
@@ -839,15 +848,15 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   }
   for (int y = ys; y < ye && !aborted && !timed_out; ++y) {
     // the loader refills the slot of row y as soon as every warp has scattered it
-    if (loader && __any_sync(kAll, mbar_test(m.bdone, par(y)))) issue_loads((y - la) + 1 + nb);
+    if (loader && __any_sync(kAll, mbar_test(bbar(y), par(y)))) issue_loads((y - la) + 1 + nb);
     const bool more = y + 1 < ye;
     uint4 dnext = make_uint4(0u, 0u, 0u, 0u);
-    if (more) dnext = phase_a(y + 1);
-    phase_c(y, dcur);
     if (more) {
+      dnext = phase_a(y + 1);
       phase_b(y + 1);
       arrive_b(y + 1);
     }
+    phase_c(y, dcur);
     dcur = dnext;
   }
 
@@ -872,8 +881,10 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
 __device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < nb; ++i) mbar_init(&m.full[i], 1);
-    mbar_init(m.bdone, blockDim.x);
-    mbar_init(m.sdone, blockDim.x);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(m.bdone + i, blockDim.x);
+      mbar_init(m.sdone + i, blockDim.x);
+    }
     fence_mbar_init();
   }
 }
