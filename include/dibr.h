@@ -227,14 +227,15 @@ dibr_status dibr_enqueue_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
  *     (the cross-bilateral rule needs a depth buffer); at most 8192 work units (rows per
  *     unit grow to fit).  Anything beyond returns DIBR_E_INVALID, with no error text.
  *   - cuda_stream: the cudaStream_t to run on (NULL: the legacy default stream).  The call
- *     returns when the batch is done; DIBR_E_TIMEOUT reports a bounded device-side wait
- *     that gave up.
+ *     is blocking: it copies the descriptors to the device, launches, waits for the batch
+ *     on cuda_stream and reads the status word before it returns; DIBR_E_TIMEOUT reports a
+ *     bounded device-side wait that gave up.
  *   - The first call on a device does a one-time set-up on that device (it looks up the
  *     device address of the scratch array); make that first call before any stream
  *     capture.
- *   - Every call shares the scratch array, and each call rewrites it: calls that overlap on
- *     the GPU (on different streams, or from different threads without ordering) race and
- *     must not be made; host-side calls are serialised by a mutex. */
+ *   - Every call shares the scratch array and rewrites it, so calls whose GPU work
+ *     overlapped would race.  Within one process that cannot happen: a mutex serialises
+ *     the calls and is held until each call's batch has completed. */
 dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const dibr_params *p,
                                          int n_params, const dibr_outputs *outs, void *cuda_stream);
 
@@ -261,6 +262,17 @@ typedef struct {
 
 dibr_status dibr_set_tuning(dibr_ctx *ctx, const dibr_tuning *t);
 dibr_status dibr_get_tuning(dibr_ctx *ctx, dibr_tuning *t);
+
+/* The limit of every bounded device-side wait of this context's launches and of its
+ * serving loop's batches, in nanoseconds (0: the default, 2 s).  The paper has no
+ * counterpart.  The kernels wait on data and on one another only with such a limit; a wait
+ * that gives up sets the context's status word, the launch unwinds after letting its own
+ * copies in flight land (that wait always uses the full 2 s), and the call -- or every
+ * frame of the served batch -- returns DIBR_E_TIMEOUT.  The context stays usable: the
+ * status word is cleared once reported.  A very small limit makes waits that would have
+ * succeeded give up, which is how the tests exercise this path without any fault.
+ * DIBR_E_INVALID if ctx is NULL. */
+dibr_status dibr_set_wait_limit(dibr_ctx *ctx, uint64_t limit_ns);
 
 /* ------------------------------------------------------------------ serving loop ---
  * Concurrent video streams with continuous batching: frames submitted on any open

@@ -183,6 +183,38 @@ def dibr_rows(img, p, y0, y1, want=("anaglyph", "left", "right")):
     return outs
 
 
+def alloc_outputs(H, W, want):
+    """Zeroed output arrays of the oracle's layout, for dibr_rows_into."""
+    return _alloc_outputs(H, W, want)[0]
+
+
+def dibr_rows_into(img, p, y0, y1, outs):
+    """Rows [y0, y1) of the whole pipeline written into the given full-size output arrays
+    (from alloc_outputs); disjoint row ranges may be computed by concurrent threads."""
+    img = _check_img(img)
+    H, W, _ = img.shape
+    co = _Outputs(*[_ptr(outs.get(n)) for n in OUTPUT_NAMES], 3 * W, W)
+    cp = _cparams(p)
+    rc = lib().or_dibr_rows(_ptr(img), W, H, 3 * W, C.byref(cp), C.byref(co), y0, y1)
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments")
+    return outs
+
+
+def dibr_parallel(img, p, want=("anaglyph", "left", "right"), threads=None, band=64):
+    """The whole pipeline for one image computed band by band on several host threads
+    (the oracle's row-band entry point; every band is computed exactly as in dibr)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    img = _check_img(img)
+    H, W, _ = img.shape
+    outs = alloc_outputs(H, W, want)
+    n = threads or max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=n) as ex:
+        list(ex.map(lambda y: dibr_rows_into(img, p, y, min(H, y + band), outs), range(0, H, band)))
+    return outs
+
+
 def inpaint2d(view, damaged, block=32, block_h=None):
     """The iterative 2-D block inpainting (Fig. 3) of one view; returns (result, pixels
     left damaged)."""

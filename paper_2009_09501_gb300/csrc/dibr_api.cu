@@ -504,6 +504,12 @@ dibr_status dibr_params_default(dibr_params *p) {
   return DIBR_OK;
 }
 
+dibr_status dibr_set_wait_limit(dibr_ctx *c, uint64_t limit_ns) {
+  if (!c) return DIBR_E_INVALID;
+  c->timeout_ns = limit_ns ? static_cast<unsigned long long>(limit_ns) : 2000000000ull;
+  return DIBR_OK;
+}
+
 dibr_status dibr_validate(const dibr_params *p, const dibr_image *img) {
   std::string why;
   return check_params(p, img, &why);

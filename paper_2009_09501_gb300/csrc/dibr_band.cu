@@ -44,6 +44,11 @@ namespace {
 
 constexpr uint32_t kAll = 0xFFFFFFFFu;
 
+// The wait for a CTA's own copies in flight before it exits after a failed wait: always the
+// full 2 s, whatever limit the other waits have, so that no copy lands in shared memory
+// the CTA has given up.
+constexpr unsigned long long kDrainLimitNs = 2000000000ull;
+
 // z-buffer entry: ((255 - depth) << 24) | RGB of the source, reduced with an atomic
 // minimum into a buffer initialised to kEmpty.  The smallest entry has the largest depth
 // (nearest source).  Two sources with equal depth have equal shifts and so never meet on
@@ -422,10 +427,10 @@ __device__ __forceinline__ void fill_luts(const Shm &m, const int32_t *lut_h, co
 
 // Every thread's wait on an mbarrier phase, the outcome agreed within the warp.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, unsigned long long timeout_ns) {
-  if (__all_sync(kAll, mbar_try_wait(bar, parity))) return true;
+  if (__all_sync(kAll, mbar_attempt(bar, parity, timeout_ns))) return true;
   const unsigned long long t0 = __shfl_sync(kAll, global_ns(), 0);
   while (true) {
-    if (__all_sync(kAll, mbar_try_wait(bar, parity))) return true;
+    if (__all_sync(kAll, mbar_attempt(bar, parity, timeout_ns))) return true;
     if (__shfl_sync(kAll, global_ns(), 0) - t0 > timeout_ns) return false;
   }
 }
@@ -868,7 +873,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       // let every copy this CTA issued land before its shared memory goes away
       for (int k = max(0, issued - nb); k < issued; ++k) {
         const uint32_t g = k0 + k;
-        if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, timeout_ns)) atomicOr(status, ST_TIMEOUT_DRAIN);
+        if (!mbar_wait_bounded(&m.full[g % nb], (g / nb) & 1, kDrainLimitNs)) atomicOr(status, ST_TIMEOUT_DRAIN);
       }
     }
     return false;

@@ -36,14 +36,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // try_wait with a suspend-time hint: a thread whose phase is not complete sleeps in the
 // barrier unit for up to 0.5 ms instead of spinning on issue slots.
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns = 500000u) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity), "r"(500000u)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
@@ -57,12 +57,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Waits for the phase of `parity` to complete; gives up after limit_ns nanoseconds and
 // returns false (the caller records the failure and unwinds without touching the GPU's
 // state further).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// One attempt of a bounded wait: a try_wait that may sleep up to 0.5 ms in the barrier
+// unit, or -- for limits below that -- a test that does not block, so that such a limit
+// takes effect.
+__device__ __forceinline__ bool mbar_attempt(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
+  return limit_ns < 500000ull ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity);
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_attempt(bar, parity, limit_ns)) return true;
   const unsigned long long t0 = global_ns();
   while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_attempt(bar, parity, limit_ns)) return true;
     if (global_ns() - t0 > limit_ns) return false;
   }
 }

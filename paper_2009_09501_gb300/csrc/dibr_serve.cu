@@ -67,7 +67,7 @@ constexpr int kStatusRing = 1024;  // > streams x slots: one entry per batch in 
 
 struct InFlight {  // one batched launch
   cudaEvent_t done;
-  int status_slot;  // pinned copy of the device status word after this batch
+  int status_slot;  // this batch's status word on the device and its pinned copy
   std::vector<std::pair<int, int>> frames;  // (stream id, slot)
   std::vector<Frame> meta;
   dibr_status status;
@@ -85,6 +85,10 @@ struct ServeState {
   int next_id = 1;
   uint64_t resident = 0;
   int *status_host = nullptr;  // pinned [kStatusRing]
+  int *status_ring = nullptr;  // device [kStatusRing]: one status word per batch, zeroed before it
+  int *gpu_status = nullptr;   // the private context's own status word (restored at shutdown)
+  cudaEvent_t ev_up = nullptr, ev_comp = nullptr;  // re-recorded by every batch
+  std::vector<cudaEvent_t> ev_free;                 // batch completion events for reuse (under mu)
   uint64_t batches = 0;
   bool stop = false;
   std::thread sched, compl_thread;
@@ -175,10 +179,24 @@ static void scheduler_loop(ServeState *st) {
     }
     // uploads (copy stream) -> batched launch (compute stream) -> downloads (copy stream)
     dibr_status status = DIBR_OK;
-    cudaEvent_t up = nullptr, comp = nullptr;
-    cudaEventCreateWithFlags(&up, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&comp, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    cudaEvent_t up = st->ev_up, comp = st->ev_comp;
+    b.done = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(st->mu);
+      if (!st->ev_free.empty()) {
+        b.done = st->ev_free.back();
+        st->ev_free.pop_back();
+      }
+    }
+    if (!b.done) cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    // the batch reports bounded-wait failures in a status word of its own, zeroed before its
+    // launch on the compute stream, so that one batch's failure never shows on later ones
+    b.status_slot = static_cast<int>(st->batches++ % kStatusRing);
+    int *status_word = st->status_ring + b.status_slot;
+    cudaMemsetAsync(status_word, 0, sizeof(int), st->gpu->stream);
+    st->gpu->status_dev = status_word;
+    st->gpu->timeout_ns = st->owner->timeout_ns;
+    st->gpu->prev_band = false;  // (the memset is other work on the stream)
     for (size_t f = 0; f < b.frames.size(); ++f) {
       const Frame &fr = b.meta[f];
       if (cudaMemcpy2DAsync(const_cast<uint8_t *>(imgs[f].rgb), imgs[f].pitch, fr.in.rgb, fr.in.pitch,
@@ -205,11 +223,8 @@ static void scheduler_loop(ServeState *st) {
           status = DIBR_E_CUDA;
       }
     }
-    b.status_slot = static_cast<int>(st->batches++ % kStatusRing);
-    cudaMemcpyAsync(&st->status_host[b.status_slot], st->gpu->status_dev, sizeof(int), cudaMemcpyDeviceToHost, st->d2h);
+    cudaMemcpyAsync(&st->status_host[b.status_slot], status_word, sizeof(int), cudaMemcpyDeviceToHost, st->d2h);
     cudaEventRecord(b.done, st->d2h);
-    cudaEventDestroy(up);
-    cudaEventDestroy(comp);
     b.status = status;
     {
       std::lock_guard<std::mutex> lk(st->mu);
@@ -234,13 +249,13 @@ static void completion_loop(ServeState *st) {
     cudaError_t e = cudaEventSynchronize(b.done);
     dibr_status status = b.status;
     if (e != cudaSuccess && status == DIBR_OK) status = DIBR_E_CUDA;
-    // device-side bounded waits report through the private context's status word, copied
-    // behind the batch's downloads (the word is sticky: later batches report it too)
+    // device-side bounded waits report through the batch's own status word, copied behind
+    // the batch's downloads
     if (status == DIBR_OK && st->status_host[b.status_slot] != 0) status = DIBR_E_TIMEOUT;
     const uint64_t t = now_ns();
-    cudaEventDestroy(b.done);
     {
       std::lock_guard<std::mutex> lk(st->mu);
+      st->ev_free.push_back(b.done);
       for (size_t f = 0; f < b.frames.size(); ++f) {
         auto it = st->streams.find(b.frames[f].first);
         if (it != st->streams.end()) {
@@ -283,12 +298,26 @@ static dibr_status ensure_serving(dibr_ctx *c) {
     return s;
   }
   st->gpu->tuning = c->tuning;
+  st->gpu_status = st->gpu->status_dev;
+  st->status_ring = static_cast<int *>(st->gpu->dev_alloc(sizeof(int) * kStatusRing));
+  if (!st->status_ring) {
+    dibr_destroy(st->gpu);
+    delete st;
+    c->set_error("device allocation of the serving status words failed");
+    return DIBR_E_NOMEM;
+  }
   if (cudaStreamCreateWithFlags(&st->h2d, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&st->d2h, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&st->ev_up, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&st->ev_comp, cudaEventDisableTiming) != cudaSuccess ||
       cudaHostAlloc(reinterpret_cast<void **>(&st->status_host), sizeof(int) * kStatusRing, cudaHostAllocDefault) !=
           cudaSuccess) {
     if (st->h2d) cudaStreamDestroy(st->h2d);
     if (st->d2h) cudaStreamDestroy(st->d2h);
+    if (st->ev_up) cudaEventDestroy(st->ev_up);
+    if (st->ev_comp) cudaEventDestroy(st->ev_comp);
+    cudaStreamSynchronize(st->gpu->stream);
+    st->gpu->dev_free(st->status_ring);
     dibr_destroy(st->gpu);
     delete st;
     return DIBR_E_CUDA;
@@ -327,6 +356,12 @@ void dibr_ctx::shutdown_serving() {
   cudaStreamDestroy(st->h2d);
   cudaStreamDestroy(st->d2h);
   cudaFreeHost(st->status_host);
+  for (cudaEvent_t e : st->ev_free) cudaEventDestroy(e);
+  cudaEventDestroy(st->ev_up);
+  cudaEventDestroy(st->ev_comp);
+  cudaStreamSynchronize(st->gpu->stream);
+  st->gpu->dev_free(st->status_ring);
+  st->gpu->status_dev = st->gpu_status;
   dibr_destroy(st->gpu);
   delete st;
   serve = nullptr;

@@ -29,7 +29,7 @@ SYMBOLS = ("dibr_params_default", "dibr_validate", "dibr_shift_tables", "dibr_cr
            "dibr_destroy", "dibr_last_error", "dibr_stream", "dibr_synthesize_image",
            "dibr_enqueue_image", "dibr_synchronize", "dibr_synthesize_batch", "dibr_enqueue_batch",
            "dibr_open_stream", "dibr_submit_frame", "dibr_poll", "dibr_close_stream",
-           "dibr_set_tuning", "dibr_get_tuning", "dibr_synthesize_batch_static")
+           "dibr_set_tuning", "dibr_get_tuning", "dibr_synthesize_batch_static", "dibr_set_wait_limit")
 
 
 class dibr_params(C.Structure):
@@ -117,6 +117,7 @@ def load(build_if_missing=True):
         "dibr_get_tuning": (C.c_int, [ctx, P(dibr_tuning)]),
         "dibr_synthesize_batch_static": (C.c_int, [C.c_int, P(dibr_image), P(dibr_params), C.c_int,
                                                    P(dibr_outputs), C.c_void_p]),
+        "dibr_set_wait_limit": (C.c_int, [ctx, C.c_uint64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -204,6 +205,10 @@ def dibr_get_tuning(ctx, t):
     return _fn("dibr_get_tuning")(ctx, C.byref(t))
 
 
+def dibr_set_wait_limit(ctx, limit_ns):
+    return _fn("dibr_set_wait_limit")(ctx, limit_ns)
+
+
 def dibr_synthesize_batch_static(n, imgs, p, n_params, outs, stream):
     return _fn("dibr_synthesize_batch_static")(n, imgs, p, n_params, outs, stream)
 
@@ -279,12 +284,19 @@ def outputs_struct(outs, pitch=None, depth_pitch=None):
 class Context:
     """Owns one dibr_ctx.  Raises DibrError on any non-OK status."""
 
-    def __init__(self, device=0, stream=None, mem_budget_bytes=0, max_streams=0, max_batch=0):
+    def __init__(self, device=0, stream=None, mem_budget_bytes=0, max_streams=0, max_batch=0,
+                 alloc=None, free=None):
+        """alloc(nbytes) -> device address (0: failure) and free(address): the context's
+        device allocations go through them (both or neither)."""
         cfg = dibr_config()
         cfg.device = device
         cfg.mem_budget_bytes = mem_budget_bytes
         cfg.max_streams, cfg.max_batch = max_streams, max_batch
         cfg.cuda_stream = stream
+        if alloc is not None or free is not None:
+            # the callbacks must outlive the context
+            self._hooks = (ALLOC_FN(lambda n, user: alloc(n) or None), FREE_FN(lambda ptr, user: free(ptr)))
+            cfg.alloc, cfg.free = self._hooks
         self._ctx = C.c_void_p()
         st = dibr_create(cfg, self._ctx)
         if st != DIBR_OK:
@@ -370,6 +382,10 @@ class Context:
         t = dibr_tuning()
         self.check(dibr_get_tuning(self._ctx, t))
         return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def set_wait_limit(self, limit_ns):
+        """Limit of the device-side bounded waits in ns (0: the default 2 s)."""
+        return self.check(dibr_set_wait_limit(self._ctx, limit_ns))
 
     def close_stream(self, sid):
         return self.check(dibr_close_stream(self._ctx, sid))

@@ -199,6 +199,18 @@ def batch_parallax(width):
     return int(round(0.025 * width))
 
 
+_POOL = {}
+
+
+def batch_pool():
+    """One frame per size class of the batched workload, {(W, H): (H, W, 3) uint8}: the
+    images the 64-image seeded mix (batch_sizes) is made of."""
+    if not _POOL:
+        for i, (W, H) in enumerate(BATCH_CLASSES):
+            _POOL[(W, H)] = Scene(W, H, 2009_09501 + 4 + i, 40, "gauss8").frame(0)
+    return _POOL
+
+
 def stream_scene(stream_index, width, height, seed=2009_09501 + 5):
     """A moving scene for one stream of the serving workload."""
     return Scene(width, height, seed * 16 + stream_index, 40, "gauss8", moving=True)

@@ -73,6 +73,68 @@ def test_static_batch_matches_context_batch_twice():
                 assert np.array_equal(got, ref), (call, j, name, int((got != ref).sum()))
 
 
+def test_static_batch_equals_oracle(oracle):
+    # the same images, checked against the CPU oracle directly
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    imgs, ins, outs, prms = [], [], [], []
+    for j, ((W, H), kw, want) in enumerate(SPECS):
+        img = scenes.Scene(W, H, seed=1200 + j, n_objects=10).frame(0)
+        imgs.append(img)
+        ins.append(torch.from_numpy(img).cuda())
+        outs.append({n: torch.zeros((H, W) if n == "depth" else (H, W, 3), dtype=torch.uint8, device="cuda")
+                     for n in want})
+        prms.append(_params(kw, want))
+    n = len(SPECS)
+    imgs_c = (D.dibr_image * n)(*[D.image_struct(t) for t in ins])
+    prms_c = (D.dibr_params * n)(*prms)
+    outs_c = (D.dibr_outputs * n)(*[D.outputs_struct(o) for o in outs])
+    torch.cuda.synchronize()
+    assert D.dibr_synthesize_batch_static(n, imgs_c, prms_c, n, outs_c, None) == D.DIBR_OK
+    for j, ((W, H), kw, want) in enumerate(SPECS):
+        p = oracle.params(depth_rule=kw.get("depth_rule", 1), disparity_rule=kw.get("disparity_rule", 0),
+                          warp_mode=kw.get("warp_mode", 0), max_parallax=kw["max_parallax"])
+        ref = oracle.dibr(imgs[j], p, want=want)
+        for name in want:
+            got = outs[j][name].cpu().numpy()
+            assert np.array_equal(got, ref[name]), (j, name, int((got != ref[name]).sum()))
+
+
+def test_static_batch_unit_limit_and_widest_block(oracle):
+    # 60 frames of 7680 x 4320 (the widest block: 480 threads per CTA) and 4 of 1280 x 720:
+    # at the automatic rows per unit the list would hold 60 * 135 + 4 * 240 = 9,060 units,
+    # more than the 8,192 the scratch array holds, so the rows per unit double until it fits
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    pool = scenes.batch_pool()
+    big, small = pool[(7680, 4320)], pool[(1280, 720)]
+    tb, ts = torch.from_numpy(big).cuda(), torch.from_numpy(small).cuda()
+    ins = [tb] * 60 + [ts] * 4
+    prms = [_params(dict(max_parallax=scenes.batch_parallax(t.shape[1])), ("anaglyph",)) for t in ins]
+    outs = [{"anaglyph": torch.full_like(t, 3)} for t in ins]
+    n = len(ins)
+    imgs_c = (D.dibr_image * n)(*[D.image_struct(t) for t in ins])
+    prms_c = (D.dibr_params * n)(*prms)
+    outs_c = (D.dibr_outputs * n)(*[D.outputs_struct(o) for o in outs])
+    torch.cuda.synchronize()
+    assert D.dibr_synthesize_batch_static(n, imgs_c, prms_c, n, outs_c, None) == D.DIBR_OK
+    # the context-based batch on two of the same entries, byte for byte, and the oracle
+    with D.Context(device=0) as ctx:
+        ref_outs = [{"anaglyph": torch.zeros_like(ins[j])} for j in (0, 63)]
+        ctx.synthesize_batch([ins[0], ins[63]], [prms[0], prms[63]], ref_outs)
+    for j, r in zip((0, 63), ref_outs):
+        assert torch.equal(outs[j]["anaglyph"], r["anaglyph"]), j
+    refs = {w: oracle.dibr_parallel(img, oracle.params(max_parallax=scenes.batch_parallax(w)), want=("anaglyph",))["anaglyph"]
+            for w, img in ((7680, big), (1280, small))}
+    for j, o in enumerate(outs):
+        got = o["anaglyph"].cpu().numpy()
+        assert np.array_equal(got, refs[got.shape[1]]), (j, int((got != refs[got.shape[1]]).sum()))
+
+
 def test_static_batch_rejects_what_it_cannot_do_without_allocating():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
