@@ -295,9 +295,29 @@ def bench_batch(D, torch, ctx, stream, n=64):
 
     t_batch = timed(lambda: ctx.enqueue_batch(ins, prms, outs))
     t_single = timed(lambda: [ctx.enqueue_image(i, q, o) for i, q, o in zip(ins, prms, outs)])
+    # the library's autotuner on this batch, then the same batched call with its choices
+    with D.Context(device=torch.cuda.current_device()) as tctx:
+        plans = tctx.autotune_batch(ins, prms, outs, reps=2)
+        tstream = torch.cuda.ExternalStream(D.dibr_stream(tctx.handle))
+
+        def timed_t(fn, reps=5):
+            fn()
+            tctx.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(tstream)
+            for _ in range(reps):
+                fn()
+            e1.record(tstream)
+            tctx.synchronize()
+            return e0.elapsed_time(e1) / reps / 1000.0
+
+        t_tuned = timed_t(lambda: tctx.enqueue_batch(ins, prms, outs))
     return {"images": n, "megapixels": pixels / 1e6, "frames_per_s_batched": n / t_batch,
+            "frames_per_s_batched_autotuned": n / t_tuned,
             "frames_per_s_per_image_launches": n / t_single, "speedup": t_single / t_batch,
-            "gb_per_s_batched": pixels * 6 / t_batch / 1e9, "sizes": "seeded mix of %s" % list(scenes.BATCH_CLASSES)}
+            "speedup_autotuned": t_single / t_tuned,
+            "gb_per_s_batched": pixels * 6 / t_batch / 1e9, "gb_per_s_batched_autotuned": pixels * 6 / t_tuned / 1e9,
+            "autotuned_plans": plans, "sizes": "seeded mix of %s" % list(scenes.BATCH_CLASSES)}
 
 
 def bench_inpaint(D, torch, ctx, stream, reps=200):

@@ -211,6 +211,27 @@ dibr_status dibr_synthesize_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
 dibr_status dibr_enqueue_batch(dibr_ctx *ctx, int n, const dibr_image *imgs,
                                const dibr_params *p, int n_params, const dibr_outputs *outs);
 
+/* Autotuner of the batched launches (the paper has no counterpart; it changes speed,
+ * never results).  The images are grouped by size class -- the block width of their rows,
+ * one thread per 16 columns rounded up to whole warps -- and each class is run alone
+ * (reps timed repetitions after one warm-up, CUDA events on the context's stream) under
+ * every candidate plan: a band launch of its own per image, or the shared persistent
+ * launch with rows per work unit in {automatic, 2, 4, 8, 16, 32, 64}, CTAs per SM
+ * {automatic, 1} and ring slots {automatic, 4}.  The fastest plan of each class is kept in
+ * the context and used by every later dibr_synthesize_batch / dibr_enqueue_batch (and
+ * serving batch) whose images fall in that class, where the matching dibr_set_tuning
+ * knob is automatic.  All buffers must be device memory; the outputs are written (with
+ * the final results) by the timed runs.  Blocking. */
+dibr_status dibr_autotune_batch(dibr_ctx *ctx, int n, const dibr_image *imgs, const dibr_params *p,
+                                int n_params, const dibr_outputs *outs, int reps);
+
+/* The autotuner's per-class choices as a JSON file ({"batch_classes": [{"block_threads",
+ * "rows_per_unit", "ctas_per_sm", "ring_slots", "own_launch"}, ...]}), written by
+ * dibr_tuning_save and read back (replacing the context's choices) by dibr_tuning_load.
+ * DIBR_E_INVALID if the file cannot be written / read or an entry is malformed. */
+dibr_status dibr_tuning_save(dibr_ctx *ctx, const char *path);
+dibr_status dibr_tuning_load(dibr_ctx *ctx, const char *path);
+
 /* Batched synthesis that allocates nothing.  The paper has no counterpart: this serves
  * callers that may not allocate memory at the time they call, for example an application
  * that reserves its whole device-memory budget at start-up and forbids allocation later,

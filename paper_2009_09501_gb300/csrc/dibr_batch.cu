@@ -8,6 +8,8 @@
 // launch per block-width group) take units from a device counter until none is left, so
 // the launches balance themselves over images of any mix of sizes.
 #include <algorithm>
+#include <cstdio>
+#include <map>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -72,7 +74,9 @@ dibr_status dibr_ctx::enqueue_batch_device(int n, const dibr_image *imgs, const 
     BatchClass c[1];
     const bool fits = plan_batch_classes(1, &w, &rb, lim, &cl, c) == 1;
     const int64_t slots = static_cast<int64_t>(num_sms) * (fits ? c[0].per : 1);
-    const bool big = fits && tuning.rows_per_unit == 0 && imgs[i].height >= kOwnLaunchRows * slots;
+    bool big = fits && tuning.rows_per_unit == 0 && imgs[i].height >= kOwnLaunchRows * slots;
+    const auto t = class_tune.find(block_of(w));
+    if (fits && tuning.rows_per_unit == 0 && t != class_tune.end() && t->second.own >= 0) big = t->second.own == 1;
     (big ? own : shared).push_back(i);
   }
   dibr_status s = DIBR_OK;
@@ -168,8 +172,22 @@ dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_
     set_error("batch images too wide for shared memory");
     return DIBR_E_INVALID;
   }
+  // the autotuner's choices for tuned classes (where the context's knobs are automatic)
+  for (int c = 0; c < nclass; ++c) {
+    const auto t = class_tune.find(cls[c].nc);
+    if (t == class_tune.end()) continue;
+    BatchLimits l2 = lim;
+    if (lim.ring_slots == 0 && t->second.nb > 0) l2.ring_slots = t->second.nb;
+    if (lim.ctas_per_sm == 0 && t->second.per > 0) l2.ctas_per_sm = t->second.per;
+    if (!plan_class(cls[c], l2)) plan_class(cls[c], lim);
+  }
   order_by_area(n, widths.data(), heights.data(), order.data());
   plan_unit_rows(n, heights.data(), class_of.data(), nclass, num_sms, tuning.rows_per_unit, cls);
+  if (tuning.rows_per_unit == 0)
+    for (int c = 0; c < nclass; ++c) {
+      const auto t = class_tune.find(cls[c].nc);
+      if (t != class_tune.end() && t->second.rows > 0) cls[c].rows = t->second.rows;
+    }
 
   // --- descriptors and units, staged in pinned memory; each group's units are
   // contiguous, largest images first
@@ -295,6 +313,120 @@ dibr_status dibr_enqueue_batch(dibr_ctx *c, int n, const dibr_image *imgs, const
     }
   cudaSetDevice(c->device);
   return c->enqueue_batch_device(n, imgs, p, n_params, outs);
+}
+
+dibr_status dibr_autotune_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p, int n_params,
+                                const dibr_outputs *outs, int reps) {
+  dibr_status s = check_batch(c, n, imgs, p, n_params, outs);
+  if (s != DIBR_OK) return s;
+  for (int i = 0; i < n; ++i)
+    if (!imgs[i].on_device || !outs[i].on_device) {
+      c->set_error("dibr_autotune_batch needs device buffers");
+      return DIBR_E_INVALID;
+    }
+  if (reps < 1) reps = 1;
+  cudaSetDevice(c->device);
+  // the images of each size class (block width), timed alone under every candidate plan
+  std::map<int, std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) groups[block_of(imgs[i].width)].push_back(i);
+  std::vector<ClassTune> cands;
+  cands.push_back(ClassTune{0, 0, 0, 1});  // a band launch per image
+  for (int rows : {0, 2, 4, 8, 16, 32, 64})
+    for (int per : {0, 1})
+      for (int nb : {0, 4}) cands.push_back(ClassTune{rows, per, nb, 0});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return c->cuda_fail(cudaGetLastError(), "creating the autotuner's events");
+  }
+  for (auto &g : groups) {
+    std::vector<dibr_image> gi;
+    std::vector<dibr_params> gp;
+    std::vector<dibr_outputs> go;
+    for (int i : g.second) {
+      gi.push_back(imgs[i]);
+      gp.push_back(p[n_params == 1 ? 0 : i]);
+      go.push_back(outs[i]);
+    }
+    const int m = static_cast<int>(gi.size());
+    float best = -1.f;
+    ClassTune pick;
+    for (const ClassTune &cand : cands) {
+      c->class_tune[g.first] = cand;
+      if ((s = c->enqueue_batch_device(m, gi.data(), gp.data(), m, go.data())) != DIBR_OK) break;  // warm-up
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps && s == DIBR_OK; ++r) s = c->enqueue_batch_device(m, gi.data(), gp.data(), m, go.data());
+      cudaEventRecord(e1, c->stream);
+      if (s != DIBR_OK) break;
+      if ((s = c->read_status()) != DIBR_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best < 0.f || ms < best) {
+        best = ms;
+        pick = cand;
+      }
+    }
+    if (s != DIBR_OK) {
+      c->class_tune.erase(g.first);
+      break;
+    }
+    c->class_tune[g.first] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+dibr_status dibr_tuning_save(dibr_ctx *c, const char *path) {
+  if (!c || !path) return DIBR_E_INVALID;
+  FILE *f = std::fopen(path, "w");
+  if (!f) {
+    c->set_error("cannot write %s", path);
+    return DIBR_E_INVALID;
+  }
+  std::fprintf(f, "{\"batch_classes\": [");
+  bool first = true;
+  for (const auto &kv : c->class_tune) {
+    std::fprintf(f, "%s\n  {\"block_threads\": %d, \"rows_per_unit\": %d, \"ctas_per_sm\": %d, \"ring_slots\": %d, "
+                 "\"own_launch\": %d}",
+                 first ? "" : ",", kv.first, kv.second.rows, kv.second.per, kv.second.nb, kv.second.own);
+    first = false;
+  }
+  std::fprintf(f, "\n]}\n");
+  const bool ok = std::fclose(f) == 0;
+  return ok ? DIBR_OK : DIBR_E_INVALID;
+}
+
+dibr_status dibr_tuning_load(dibr_ctx *c, const char *path) {
+  if (!c || !path) return DIBR_E_INVALID;
+  FILE *f = std::fopen(path, "r");
+  if (!f) {
+    c->set_error("cannot read %s", path);
+    return DIBR_E_INVALID;
+  }
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+  std::fclose(f);
+  // entries as dibr_tuning_save writes them; anything else is rejected
+  std::map<int, ClassTune> table;
+  size_t pos = 0;
+  while ((pos = text.find("{\"block_threads\":", pos)) != std::string::npos) {
+    int nc, rows, per, nb, own;
+    if (std::sscanf(text.c_str() + pos,
+                    "{\"block_threads\": %d, \"rows_per_unit\": %d, \"ctas_per_sm\": %d, \"ring_slots\": %d, "
+                    "\"own_launch\": %d}",
+                    &nc, &rows, &per, &nb, &own) != 5 ||
+        nc < 32 || nc > kMaxConsumers || nc % 32 || rows < 0 || per < 0 || nb < 0 || nb > kMaxRing || own < -1 || own > 1) {
+      c->set_error("%s: malformed tuning entry", path);
+      return DIBR_E_INVALID;
+    }
+    table[nc] = ClassTune{rows, per, nb, own};
+    ++pos;
+  }
+  c->class_tune = table;
+  return DIBR_OK;
 }
 
 dibr_status dibr_synthesize_batch(dibr_ctx *c, int n, const dibr_image *imgs, const dibr_params *p, int n_params,

@@ -4,6 +4,7 @@
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -20,6 +21,15 @@ struct DevBuf {
 };
 
 struct ServeState;  // dibr_serve.cu
+
+// A batched launch plan chosen by the autotuner for one size class (the block width, in
+// threads, of the images' rows); a zero field (own: -1) keeps the automatic choice.
+struct ClassTune {
+  int rows = 0;  // rows per work unit
+  int per = 0;   // CTAs per SM at most
+  int nb = 0;    // ring slots at most
+  int own = -1;  // 1: every image of the class in a band launch of its own; 0: shared launches
+};
 
 }  // namespace dibr
 
@@ -39,6 +49,7 @@ struct dibr_ctx {
   int *status_dev = nullptr;
   unsigned long long timeout_ns = 2000000000ull;  // 2 s per bounded device-side wait
   dibr_tuning tuning{};      // zero fields: automatic
+  std::map<int, dibr::ClassTune> class_tune;  // per block width: the autotuner's choices
   uint64_t launches = 0;     // kernels launched by this context
 
   std::mutex err_mu;

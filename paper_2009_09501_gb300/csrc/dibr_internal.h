@@ -192,6 +192,30 @@ struct BatchLimits {
 inline int chunks_of(int width) { return (width + kChunk - 1) / kChunk; }
 inline int block_of(int width) { return round_up(chunks_of(width), 32); }
 
+// Ring depth and CTAs per SM of one group (nc, nch_max and srow set): the deepest ring at
+// the most CTAs per SM within the limits.  Returns false if no plan fits.
+inline bool plan_class(BatchClass &k, const BatchLimits &lim) {
+  const int max_nb = lim.ring_slots > 0 ? (lim.ring_slots < 4 ? 4 : lim.ring_slots < kMaxRing ? lim.ring_slots : kMaxRing)
+                                        : kMaxRing;
+  const int by_regs = 65536 / (k.nc * 128), by_threads = 2048 / k.nc;
+  const int max_per = by_regs < by_threads ? by_regs : by_threads;
+  k.per = 0;
+  for (int nb = 4; nb <= max_nb; ++nb) {
+    const int tot = band_smem_layout(nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
+    if (tot > lim.max_smem) continue;
+    int per = lim.smem_per_sm / (tot + 1024);
+    if (per > max_per) per = max_per;
+    if (lim.ctas_per_sm > 0 && per > lim.ctas_per_sm) per = lim.ctas_per_sm;
+    if (per >= 1 && per >= k.per) {  // the deepest ring at the best CTAs per SM
+      k.per = per;
+      k.nb = nb;
+    }
+  }
+  if (k.per < 1) return false;
+  k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
+  return true;
+}
+
 // Groups the n images by block width (widest first), plans each group's ring and CTAs per
 // SM, and sets class_of[i].  Returns the number of groups, or -1 if some group fits no plan.
 inline int plan_batch_classes(int n, const int *width, const int *row_bytes, const BatchLimits &lim,
@@ -217,27 +241,8 @@ inline int plan_batch_classes(int n, const int *width, const int *row_bytes, con
     if (nch > cls[c].nch_max) cls[c].nch_max = nch;
     if (round_up(need, 128) > cls[c].srow) cls[c].srow = round_up(need, 128);
   }
-  const int max_nb = lim.ring_slots > 0 ? (lim.ring_slots < 4 ? 4 : lim.ring_slots < kMaxRing ? lim.ring_slots : kMaxRing)
-                                        : kMaxRing;
-  for (int c = 0; c < nclass; ++c) {
-    BatchClass &k = cls[c];
-    const int by_regs = 65536 / (k.nc * 128), by_threads = 2048 / k.nc;
-    const int max_per = by_regs < by_threads ? by_regs : by_threads;
-    k.per = 0;
-    for (int nb = 4; nb <= max_nb; ++nb) {
-      const int tot = band_smem_layout(nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
-      if (tot > lim.max_smem) continue;
-      int per = lim.smem_per_sm / (tot + 1024);
-      if (per > max_per) per = max_per;
-      if (lim.ctas_per_sm > 0 && per > lim.ctas_per_sm) per = lim.ctas_per_sm;
-      if (per >= 1 && per >= k.per) {  // the deepest ring at the best CTAs per SM
-        k.per = per;
-        k.nb = nb;
-      }
-    }
-    if (k.per < 1) return -1;
-    k.smem = band_smem_layout(k.nb, k.srow, k.nch_max, k.nc / 32, lim.zguard).total;
-  }
+  for (int c = 0; c < nclass; ++c)
+    if (!plan_class(cls[c], lim)) return -1;
   return nclass;
 }
 

@@ -29,7 +29,8 @@ SYMBOLS = ("dibr_params_default", "dibr_validate", "dibr_shift_tables", "dibr_cr
            "dibr_destroy", "dibr_last_error", "dibr_stream", "dibr_synthesize_image",
            "dibr_enqueue_image", "dibr_synchronize", "dibr_synthesize_batch", "dibr_enqueue_batch",
            "dibr_open_stream", "dibr_submit_frame", "dibr_poll", "dibr_close_stream",
-           "dibr_set_tuning", "dibr_get_tuning", "dibr_synthesize_batch_static", "dibr_set_wait_limit")
+           "dibr_set_tuning", "dibr_get_tuning", "dibr_synthesize_batch_static", "dibr_set_wait_limit",
+           "dibr_autotune_batch", "dibr_tuning_save", "dibr_tuning_load")
 
 
 class dibr_params(C.Structure):
@@ -118,6 +119,10 @@ def load(build_if_missing=True):
         "dibr_synthesize_batch_static": (C.c_int, [C.c_int, P(dibr_image), P(dibr_params), C.c_int,
                                                    P(dibr_outputs), C.c_void_p]),
         "dibr_set_wait_limit": (C.c_int, [ctx, C.c_uint64]),
+        "dibr_autotune_batch": (C.c_int, [ctx, C.c_int, P(dibr_image), P(dibr_params), C.c_int, P(dibr_outputs),
+                                          C.c_int]),
+        "dibr_tuning_save": (C.c_int, [ctx, C.c_char_p]),
+        "dibr_tuning_load": (C.c_int, [ctx, C.c_char_p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -209,6 +214,18 @@ def dibr_set_wait_limit(ctx, limit_ns):
     return _fn("dibr_set_wait_limit")(ctx, limit_ns)
 
 
+def dibr_autotune_batch(ctx, n, imgs, p, n_params, outs, reps):
+    return _fn("dibr_autotune_batch")(ctx, n, imgs, p, n_params, outs, reps)
+
+
+def dibr_tuning_save(ctx, path):
+    return _fn("dibr_tuning_save")(ctx, path.encode())
+
+
+def dibr_tuning_load(ctx, path):
+    return _fn("dibr_tuning_load")(ctx, path.encode())
+
+
 def dibr_synthesize_batch_static(n, imgs, p, n_params, outs, stream):
     return _fn("dibr_synthesize_batch_static")(n, imgs, p, n_params, outs, stream)
 
@@ -281,6 +298,12 @@ def outputs_struct(outs, pitch=None, depth_pitch=None):
     return o
 
 
+def block_threads(width):
+    """The size class of an image in batched launches: threads per block for its rows (one
+    per 16 columns, rounded up to whole warps)."""
+    return ((width + 15) // 16 + 31) // 32 * 32
+
+
 class Context:
     """Owns one dibr_ctx.  Raises DibrError on any non-OK status."""
 
@@ -346,6 +369,29 @@ class Context:
         Pa = (dibr_params * len(params))(*params)
         O = (dibr_outputs * max(n, 1))(*[outputs_struct(o) for o in outs])
         return n, I, Pa, len(params), O
+
+    def autotune_batch(self, imgs, params, outs, reps=3):
+        """Times candidate launch plans per size class on this batch (device buffers) and
+        keeps the fastest in the context; returns the chosen plans."""
+        self._after_torch(imgs, outs)
+        self.check(dibr_autotune_batch(self._ctx, *self._batch_args(imgs, params, outs), reps))
+        import json
+        import os
+        import tempfile
+        fd, path = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        try:
+            self.check(dibr_tuning_save(self._ctx, path))
+            with open(path) as f:
+                return json.load(f)["batch_classes"]
+        finally:
+            os.unlink(path)
+
+    def save_tuning(self, path):
+        return self.check(dibr_tuning_save(self._ctx, path))
+
+    def load_tuning(self, path):
+        return self.check(dibr_tuning_load(self._ctx, path))
 
     def synthesize_batch(self, imgs, params, outs):
         self._after_torch(imgs, outs)

@@ -270,3 +270,42 @@ def test_serving_workload5_streams_sample(ctx, torch, oracle):
             assert np.array_equal(out[y], ref), (sid, f, y)
     for s in sids:
         ctx.close_stream(s)
+
+
+# ------------------------------------------------------------------------- autotuner
+def test_autotuned_batches_equal_the_oracle_and_persist(torch, oracle, tmp_path):
+    sizes = [(1920, 1080), (1920, 1080), (1280, 720), (3840, 2160), (333, 97), (1280, 720)]
+    imgs, ins, prms = [], [], []
+    for j, (W, H) in enumerate(sizes):
+        img = scenes.Scene(W, H, seed=1500 + j, n_objects=16).frame(0)
+        imgs.append(img)
+        ins.append(torch.from_numpy(img).cuda())
+        prms.append(gparams(dict(max_parallax=scenes.batch_parallax(W)), ("anaglyph", "left")))
+    refs = [oracle.dibr_parallel(imgs[j], oparams(oracle, dict(max_parallax=scenes.batch_parallax(W))),
+                                 want=("anaglyph", "left")) for j, (W, H) in enumerate(sizes)]
+    mk = lambda: [{n: torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda") for n in ("anaglyph", "left")}
+                  for (W, H) in sizes]
+    path = str(tmp_path / "tuning.json")
+    with D.Context(device=0) as c:
+        outs = mk()
+        plans = c.autotune_batch(ins, prms, outs, reps=1)
+        classes = sorted({D.block_threads(W) for (W, H) in sizes})
+        assert sorted(p["block_threads"] for p in plans) == classes
+        for j in range(len(sizes)):  # the tuner's own runs leave the final results
+            check(outs[j], refs[j], "tuner run image %d" % j)
+        outs = mk()
+        c.synthesize_batch(ins, prms, outs)
+        for j in range(len(sizes)):
+            check(outs[j], refs[j], "tuned batch image %d" % j)
+        c.save_tuning(path)
+    with D.Context(device=0) as c2:
+        c2.load_tuning(path)
+        outs = mk()
+        c2.synthesize_batch(ins, prms, outs)
+        for j in range(len(sizes)):
+            check(outs[j], refs[j], "reloaded tuning image %d" % j)
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"batch_classes": [{"block_threads": 33, "rows_per_unit": 1, "ctas_per_sm": 0, '
+                       '"ring_slots": 0, "own_launch": 0}]}')
+        with pytest.raises(D.DibrError):
+            c2.load_tuning(str(bad))
