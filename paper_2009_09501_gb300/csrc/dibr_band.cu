@@ -301,26 +301,34 @@ __device__ __forceinline__ uint32_t filled_mask(const uint32_t (&k)[16]) {
   return m;
 }
 
-// Left to right: every entry whose bit of m is clear takes the last entry with its bit set
-// (c: the entry carried in).
-__device__ __forceinline__ void carry_right(uint32_t (&k)[16], uint32_t m, uint32_t c) {
+// Left to right over the 16 entries of both views (two independent chains): an empty
+// entry takes the last filled entry before it (c0, c1: the entries carried in).  Columns
+// past the row's end come last, so whatever they hold changes no column of the row.
+__device__ __forceinline__ void carry_right2(uint32_t (&k0)[16], uint32_t (&k1)[16], uint32_t c0, uint32_t c1) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    asm("{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.u32 p, t, 0;\n\t"
-        "selp.b32 %1, %0, %1, p;\n\tmov.b32 %0, %1;\n\t}"
-        : "+r"(k[j]), "+r"(c) : "r"(m), "r"(1u << j));
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, -1;\n\tselp.b32 %1, %0, %1, p;\n\tmov.b32 %0, %1;\n\t}"
+        : "+r"(k0[j]), "+r"(c0));
+    asm("{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %0, -1;\n\tselp.b32 %1, %0, %1, p;\n\tmov.b32 %0, %1;\n\t}"
+        : "+r"(k1[j]), "+r"(c1));
   }
 }
 
-// Right to left: c carries the last entry with its bit set (c: the entry carried in), and
-// an entry whose bit is clear takes c where c is strictly farther (c > (k | 0xFFFFFF)).
-__device__ __forceinline__ void carry_left_farther(uint32_t (&k)[16], uint32_t m, uint32_t c) {
+// Right to left over both views: c carries the last entry whose bit of m is set (the
+// filled targets of the row; c0, c1: the entries carried in), and an entry whose bit is
+// clear takes c where c is strictly farther (c > (k | 0xFFFFFF)).
+__device__ __forceinline__ void carry_left_farther2(uint32_t (&k0)[16], uint32_t (&k1)[16], uint32_t m0, uint32_t m1,
+                                                    uint32_t c0, uint32_t c1) {
 #pragma unroll
   for (int j = 15; j >= 0; --j) {
     asm("{\n\t.reg .pred p, q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.u32 p, t, 0;\n\t"
         "selp.b32 %1, %0, %1, p;\n\tor.b32 t, %0, 0xFFFFFF;\n\tsetp.gt.u32 q, %1, t;\n\t"
         "selp.b32 %0, %1, %0, q;\n\t}"
-        : "+r"(k[j]), "+r"(c) : "r"(m), "r"(1u << j));
+        : "+r"(k0[j]), "+r"(c0) : "r"(m0), "r"(1u << j));
+    asm("{\n\t.reg .pred p, q;\n\t.reg .b32 t;\n\tand.b32 t, %2, %3;\n\tsetp.ne.u32 p, t, 0;\n\t"
+        "selp.b32 %1, %0, %1, p;\n\tor.b32 t, %0, 0xFFFFFF;\n\tsetp.gt.u32 q, %1, t;\n\t"
+        "selp.b32 %0, %1, %0, q;\n\t}"
+        : "+r"(k1[j]), "+r"(c1) : "r"(m1), "r"(1u << j));
   }
 }
 
@@ -767,12 +775,15 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       mbar_arrive(sbar(y));
       // entries from outside the warp, for lanes whose leading (trailing) holes have no
       // filled target below (above) them in the warp: the nearest warp's last (first)
-      // filled entry, from the summaries
+      // filled entry, from the summaries -- only where a warp below (above) exists: the
+      // holes at the row's ends need nothing from the other warps
       bool need = false;
+      const bool below_exists = warp_lo > 0, above_exists = warp_hi < W;
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
         const uint32_t lower = lanes[v] & ltm, upper = lanes[v] & gtm;
-        need |= active && ((lower == 0u && !(mm[v] & 1u)) || (upper == 0u && !((mm[v] >> ((npx - 1) & 15)) & 1u)));
+        need |= active && ((below_exists && lower == 0u && !(mm[v] & 1u)) ||
+                           (above_exists && upper == 0u && !((mm[v] >> ((npx - 1) & 15)) & 1u)));
       }
       uint32_t wle[2] = {0u, 0u}, wre[2] = {0u, 0u};
       bool wlh[2] = {false, false}, wrh[2] = {false, false};
@@ -801,21 +812,30 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       // (255 - depth) << 24 | colour, so "c strictly farther than k" is the unsigned
       // compare c > (k | 0xFFFFFF)).  A missing right entry carries in as 0, which is never
       // strictly farther; holes with no filled target on their left (the row's start)
-      // carry in the first filled entry on their right from the start.
+      // carry in the first filled entry on their right from the start.  Both views'
+      // sweeps run interleaved.
+      uint32_t lin[2], rin[2];
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
         const uint32_t lower = lanes[v] & ltm, upper = lanes[v] & gtm, mk = mm[v];
-        const uint32_t rin = upper ? cr[v] : wre[v];
-        const uint32_t lin = lower ? cl[v] : (wlh[v] ? wle[v] : (mk ? fe[v] : rin));
-        carry_right(k[v], mk, lin);
-        carry_left_farther(k[v], mk, rin);
+        rin[v] = upper ? cr[v] : wre[v];
+        lin[v] = lower ? cl[v] : (wlh[v] ? wle[v] : (mk ? fe[v] : rin[v]));
         hole[v] = ~mk & rowmask;
-        if (lanes[v] == 0u && !wlh[v] && !wrh[v]) {  // (warp-uniform)
-#pragma unroll
-          for (int j = 0; j < 16; ++j) k[v][j] = active ? rgb_at_global(grow, min(x0 + j, W - 1)) : 0u;
-        }
-        emit_view(v, k[v]);
       }
+      carry_right2(k[0], k[1], lin[0], lin[1]);
+      carry_left_farther2(k[0], k[1], mm[0], mm[1], rin[0], rin[1]);
+      // a view of a row without any filled target shows the input row (warp-uniform)
+      const bool none0 = lanes[0] == 0u && !wlh[0] && !wrh[0], none1 = lanes[1] == 0u && !wlh[1] && !wrh[1];
+      if (none0 || none1) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t c = active ? rgb_at_global(grow, min(x0 + j, W - 1)) : 0u;
+          if (none0) k[0][j] = c;
+          if (none1) k[1][j] = c;
+        }
+      }
+      emit_view(0, k[0]);
+      emit_view(1, k[1]);
     } else {
       // Fig. 3 literally: sample trunc(x + s(d)); out of range -> own column
       mbar_arrive(sbar(y));
