@@ -332,6 +332,10 @@ def bench_inpaint(D, torch, ctx, stream, reps=200):
         sets.append((i, {n: torch.empty((H, W, 3), dtype=torch.uint8, device="cuda") for n in OUTPUTS}))
     torch.cuda.synchronize()
     res = {}
+    # both arms with every band launch over all SMs (a frame with the 2-D fill never runs
+    # beside the next one), so that the difference is the inpainting's own time
+    fif = ctx.get_tuning()["frames_in_flight"]
+    ctx.set_tuning(frames_in_flight=1)
     for name, fill in (("row_fill", D.DIBR_FILL_ROW), ("inpaint2d", D.DIBR_FILL_INPAINT2D)):
         p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, hole_fill=fill, inpaint_block=32)
         for k in range(10):
@@ -344,6 +348,7 @@ def bench_inpaint(D, torch, ctx, stream, reps=200):
         e1.record(stream)
         ctx.synchronize()
         res[name] = e0.elapsed_time(e1) / reps * 1000.0
+    ctx.set_tuning(frames_in_flight=fif)
     return {"workload": "3840x2160, P=64, L+R+anaglyph, 2-D block inpainting (32x32 blocks) after the row fill",
             "frames_per_s": 1e6 / res["inpaint2d"], "us_per_frame": res["inpaint2d"],
             "row_fill_us_per_frame": res["row_fill"], "inpaint_overhead_us": res["inpaint2d"] - res["row_fill"],
@@ -361,6 +366,10 @@ def bench_xbf(D, torch, ctx, stream, reps=200):
             for _ in range(4)]
     torch.cuda.synchronize()
     res = {}
+    # both arms with every band launch over all SMs (a frame whose band launch reads the
+    # cross-bilateral depth never runs beside the next one)
+    fif = ctx.get_tuning()["frames_in_flight"]
+    ctx.set_tuning(frames_in_flight=1)
     for name, rule in (("binom5", D.DIBR_DEPTH_LUMA_BINOM5), ("xbf", D.DIBR_DEPTH_LUMA_XBF)):
         p = D.make_params(max_parallax=P4K, outputs=OUTPUTS, depth_rule=rule)
         for k in range(10):
@@ -373,6 +382,7 @@ def bench_xbf(D, torch, ctx, stream, reps=200):
         e1.record(stream)
         ctx.synchronize()
         res[name] = e0.elapsed_time(e1) / reps * 1000.0
+    ctx.set_tuning(frames_in_flight=fif)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     taps = sum(min(y + 2, H - 1) - max(y - 2, 0) + 1 for y in range(H)) * \
         sum(min(x + 2, W - 1) - max(x - 2, 0) + 1 for x in range(W))
@@ -559,10 +569,12 @@ def run_ours(args):
     ctx.synchronize()
     total_ms = e_start.elapsed_time(e_end)
     mean_launch_ms = total_ms / K  # average launch duration over the timed region
-    # spread of single launches, each bracketed by its own events (outside the timed region)
+    # latency of single launches on an idle GPU, each bracketed by its own events (outside
+    # the timed region; a launch on an idle stream spreads over every SM)
     n_single = min(K, 200)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_single)]
     for k in range(n_single):
+        ctx.synchronize()
         ev[k][0].record(stream)
         step(k)
         ev[k][1].record(stream)

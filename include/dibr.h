@@ -275,10 +275,17 @@ dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const di
  *                  is small (one 4K frame: 8 rows), 32 rows otherwise;
  *   host_bands     row bands of dibr_synthesize_image with host input and outputs (the
  *                  bands' uploads, kernels and downloads overlap), 1..8; automatic: 4 from
- *                  2048 rows, 2 from 512, else 1.
+ *                  2048 rows, 2 from 512, else 1;
+ *   frames_in_flight  1..16: when a frame is enqueued on the context's own stream while
+ *                  earlier work is still queued there, and it shares no buffer with the
+ *                  frame before it, its launch takes 1/n of the SM slots (in taller row
+ *                  bands), so that n consecutive frames run side by side; 1: every launch
+ *                  spreads over all SMs.  A launch on an idle stream always does.
+ *                  Automatic: 8.
  * dibr_set_tuning() rejects out-of-range values with DIBR_E_INVALID. */
 typedef struct {
     int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit, host_bands;
+    int32_t frames_in_flight;
 } dibr_tuning;
 
 dibr_status dibr_set_tuning(dibr_ctx *ctx, const dibr_tuning *t);

@@ -429,8 +429,19 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
       if (prev_out[j].hi && meets(cur_out[i], prev_out[j])) disjoint = false;  // writes what it wrote
   }
   a.overlap = disjoint ? 1 : 0;
+  // A frame enqueued behind queued work: consecutive independent frames run side by side
+  // in a share of the SM slots each, in taller row bands (fewer band start-ups, whose
+  // first input rows arrive while another frame's CTA on the SM computes), instead of
+  // one after the other across every SM.  Both CTAs of an SM must fit at once.
+  const int fif = tuning.frames_in_flight > 0 ? tuning.frames_in_flight : kFramesInFlight;
+  const int full_grid = a.grid;
+  if (disjoint && fif > 1 && per_sm >= 2 && cudaStreamQuery(stream) == cudaErrorNotReady) {
+    if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();  // (not an error)
+    a.grid = std::max(1, std::min(a.grid, (num_sms * per_sm + fif - 1) / fif));
+  }
   cudaError_t e = launch_band(a, smem, per_sm, stream);
   a.overlap = 0;
+  a.grid = full_grid;
   if (e != cudaSuccess) return cuda_fail(e, "band kernel launch");
   ++launches;
   if (!inpaint) {
@@ -605,7 +616,8 @@ dibr_status dibr_set_tuning(dibr_ctx *c, const dibr_tuning *t) {
   if (t->ring_slots < 0 || t->ring_slots > kMaxRing || (t->ring_slots > 0 && t->ring_slots < 2) ||
       t->ctas_per_sm < 0 || t->ctas_per_sm > 32 || t->load_mode < 0 || t->load_mode > 5 ||
       t->l2_prefetch < 0 || t->l2_prefetch > 2 || t->rows_per_unit < 0 || t->rows_per_unit > 4096 ||
-      t->host_bands < 0 || t->host_bands > dibr_ctx::kMaxBands) {
+      t->host_bands < 0 || t->host_bands > dibr_ctx::kMaxBands || t->frames_in_flight < 0 ||
+      t->frames_in_flight > 16) {
     c->set_error("tuning value out of range");
     return DIBR_E_INVALID;
   }

@@ -63,7 +63,8 @@ class dibr_config(C.Structure):
 
 class dibr_tuning(C.Structure):
     _fields_ = [("ring_slots", C.c_int32), ("ctas_per_sm", C.c_int32), ("load_mode", C.c_int32),
-                ("l2_prefetch", C.c_int32), ("rows_per_unit", C.c_int32), ("host_bands", C.c_int32)]
+                ("l2_prefetch", C.c_int32), ("rows_per_unit", C.c_int32), ("host_bands", C.c_int32),
+                ("frames_in_flight", C.c_int32)]
 
 
 class dibr_completion(C.Structure):

@@ -138,9 +138,10 @@ def test_batch_workload4_classes_sampled_rows(ctx, torch, oracle):
 
 def test_tuning_api_validates(ctx):
     t = ctx.get_tuning()
-    assert t == dict(ring_slots=0, ctas_per_sm=0, load_mode=0, l2_prefetch=0, rows_per_unit=0, host_bands=0)
+    assert t == dict(ring_slots=0, ctas_per_sm=0, load_mode=0, l2_prefetch=0, rows_per_unit=0, host_bands=0,
+                     frames_in_flight=0)
     for bad in [dict(load_mode=6), dict(ring_slots=9), dict(ring_slots=1), dict(l2_prefetch=3), dict(rows_per_unit=-1),
-                dict(host_bands=9), dict(host_bands=-1)]:
+                dict(host_bands=9), dict(host_bands=-1), dict(frames_in_flight=17), dict(frames_in_flight=-1)]:
         with pytest.raises(D.DibrError):
             ctx.set_tuning(**bad)
 

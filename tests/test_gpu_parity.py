@@ -394,3 +394,29 @@ def test_back_to_back_frames_overlap_only_when_independent(ctx, torch, oracle):
         assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, ref, "frame %d" % k)
     ref2 = oracle.dibr(outs[3]["left"].cpu().numpy(), oracle_params(oracle, max_parallax=P), want=("anaglyph",))
     assert_same({"anaglyph": chained["anaglyph"].cpu().numpy()}, ref2, "chained frame")
+
+
+@pytest.mark.parametrize("fif", [0, 3])
+def test_4k_frames_side_by_side(ctx, torch, oracle, fif):
+    # a dozen independent 4K frames enqueued back to back: from the second on, each is
+    # enqueued behind queued work and runs beside its neighbours in a share of the SM
+    # slots (taller row bands); every frame keeps its own outputs
+    imgs = [scenes.config_scene(2), scenes.config_scene(3)]
+    H, W = imgs[0].shape[:2]
+    prm = oracle_params(oracle, max_parallax=64)
+    refs = [oracle.dibr_parallel(im, prm, want=("anaglyph", "left", "right")) for im in imgs]
+    ins = [torch.from_numpy(im).cuda() for im in imgs]
+    outs = [{n: torch.zeros((H, W, 3), dtype=torch.uint8, device="cuda") for n in ("anaglyph", "left", "right")}
+            for _ in range(12)]
+    p = gpu_params(("anaglyph", "left", "right"), max_parallax=64)
+    ctx.set_tuning(frames_in_flight=fif)
+    try:
+        torch.cuda.synchronize()
+        lib = D.load()
+        for k in range(12):
+            assert lib.dibr_enqueue_image(ctx.handle, D.image_struct(ins[k % 2]), p, D.outputs_struct(outs[k])) == 0
+        ctx.synchronize()
+    finally:
+        ctx.set_tuning(frames_in_flight=0)
+    for k in range(12):
+        assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, refs[k % 2], "frame %d" % k)
