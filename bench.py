@@ -61,19 +61,24 @@ def whole_job_rate(units_per_rank, seconds_per_rank, world, dist=None, device="c
     return world * units_per_rank / reduce_max(seconds_per_rank, dist, device)
 
 
-def kernel_source_digest():
+BAND_SOURCES = ("dibr_band.cu", "dibr_internal.h", "dibr_ptx.cuh")
+INPAINT_SOURCES = ("dibr_inpaint.cu", "dibr_internal.h", "dibr_ptx.cuh")
+
+
+def kernel_source_digest(files=BAND_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in ("dibr_band.cu", "dibr_internal.h", "dibr_ptx.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2009_09501_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic():
-    """DRAM bytes per launch of the band kernel from the committed ncu summary, or None
-    when the kernel sources changed since it was captured."""
-    path = os.path.join(ROOT, "profiles", "band_kernel_4k_stereo.md")
+def load_profile_value(name, key, files):
+    """One figure ("- key: value" line) of a committed ncu summary under profiles/, or None
+    when the kernel's sources changed since it was captured (the summary's
+    kernel_source_digest)."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         vals = {}
         with open(path) as f:
@@ -81,11 +86,16 @@ def load_traffic():
                 if line.startswith("- ") and ":" in line:
                     k, v = line[2:].split(":", 1)
                     vals[k.strip()] = v.strip().strip("`")
-        if vals.get("kernel_source_digest") != kernel_source_digest():
+        if vals.get("kernel_source_digest") != kernel_source_digest(files):
             return None, "stale (kernel changed since the capture)"
-        return float(vals["dram_bytes_per_launch"]), "ncu capture, profiles/band_kernel_4k_stereo.md"
+        return float(vals[key]), "ncu capture, profiles/" + name
     except Exception:
         return None, "no capture"
+
+
+def load_traffic():
+    """DRAM bytes per launch of the band kernel from the committed ncu summary."""
+    return load_profile_value("band_kernel_4k_stereo.md", "dram_bytes_per_launch", BAND_SOURCES)
 
 
 def load_peaks():
@@ -349,10 +359,26 @@ def bench_inpaint(D, torch, ctx, stream, reps=200):
         ctx.synchronize()
         res[name] = e0.elapsed_time(e1) / reps * 1000.0
     ctx.set_tuning(frames_in_flight=fif)
+    # Issue-slot bound: the inpainting is bound by the issue slots its step loop and visits
+    # share (it moves 50 MB per frame: far from HBM).  Its warp instructions per 4K frame
+    # (fixed for this workload and code) come from the committed ncu summary; the floor is
+    # that count at every scheduler issuing one warp instruction per clock.
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    clock_hz = 2.07e9  # the maximum SM clock; the clocks sampled in the timed region bound it
+    peak = 4 * props.multi_processor_count * clock_hz  # warp instructions per second
+    insts, src = load_profile_value("inpaint_kernel_4k.md", "warp_instructions_per_launch", INPAINT_SOURCES)
+    over = res["inpaint2d"] - res["row_fill"]
+    roof = {"bound": "issue", "unit": "warp instructions/s", "peak": peak,
+            "peak_source": "4 schedulers x SMs x 2.07 GHz (derived)", "instructions_per_frame": insts,
+            "instructions_source": src,
+            "floor_us": insts / peak * 1e6 if insts else None,
+            "achieved": insts / (over * 1e-6) if insts and over > 0 else None,
+            "frac": insts / (over * 1e-6) / peak if insts and over > 0 else None,
+            "note": "kernel time taken as the frame time with the 2-D fill minus the frame time with the row fill"}
     return {"workload": "3840x2160, P=64, L+R+anaglyph, 2-D block inpainting (32x32 blocks) after the row fill",
             "frames_per_s": 1e6 / res["inpaint2d"], "us_per_frame": res["inpaint2d"],
-            "row_fill_us_per_frame": res["row_fill"], "inpaint_overhead_us": res["inpaint2d"] - res["row_fill"],
-            "launches_per_frame": 2}
+            "row_fill_us_per_frame": res["row_fill"], "inpaint_overhead_us": over,
+            "launches_per_frame": 3, "roofline": roof}
 
 
 def bench_xbf(D, torch, ctx, stream, reps=200):
