@@ -252,39 +252,51 @@ __device__ __forceinline__ void inpaint_block(const InpaintArgs &a, int item, ui
     // repair since their last visit); when no damaged pixel is dirty nothing can change any
     // more, which is where the figure's loop ends too (a pass that repairs nothing).  Steps
     // at which no lane has a dirty pixel to visit are skipped.
-    uint32_t dirty = own & rows;
+    // dirty damaged rows of this lane's column (always a subset of own; none past a real
+    // column)
+    const uint32_t live = col ? rows : 0u;  // the rows that can be dirty in this lane
+    uint32_t dirty = own & live;
     refresh();
     const int x2 = 2 * lane;
-    // block rows y that lane x has reached by step t: y <= t - 2x
-    auto reached = [&](int t) -> uint32_t {
+    // block rows of this lane's column visited at step t: y = t - 2x - 4p, p >= 0, y >= 0
+    auto window = [&](int t) -> uint32_t {
       const int b = t - x2;
-      return b < 0 ? 0u : b >= 31 ? 0xFFFFFFFFu : (2u << b) - 1u;
+      return b < 0 ? 0u : (0x11111111u << (b & 3)) & (b >= 31 ? 0xFFFFFFFFu : (2u << b) - 1u);
     };
     // the first step at or after t with a visit to make, over the warp (INT_MAX: none): t
     // when the lane has a dirty row it has reached (visited within 4 steps), else the first
     // visit of its lowest dirty row, 2x + y; both are max(t, 2x + lowest dirty row)
     auto next_step = [&](int t) -> int {
-      const uint32_t dd = col ? own & dirty : 0u;
-      const int n = dd ? max(t, x2 + __ffs(dd) - 1) : 0x7FFFFFFF;
+      const int n = dirty ? max(t, x2 + __ffs(dirty) - 1) : 0x7FFFFFFF;
       return __reduce_min_sync(0xffffffffu, n);
     };
-    for (int t = next_step(0); t != 0x7FFFFFFF; t = next_step(t + 1)) {
-      const int b = t - x2;
-      // damaged, dirty rows of this lane's column visited at step t: y = b - 4p, p >= 0
-      uint32_t cand = col && b >= 0 ? own & dirty & reached(t) & (0x11111111u << (b & 3)) : 0u;
-      uint32_t mine = 0;
-      while (cand) {
-        const int y = __ffs(cand) - 1;
-        cand &= cand - 1;
-        dirty &= ~(1u << y);
-        if (visit(y)) mine |= 1u << y;
+    int t = next_step(0);
+    uint32_t win = window(t);
+    while (t != 0x7FFFFFFF) {
+      uint32_t cand = dirty & win;
+      // a step with visits goes on to the next step; after a step without any, the warp
+      // jumps to the first step with a visit to make (or ends)
+      if (__any_sync(0xffffffffu, cand != 0u)) {
+        uint32_t mine = 0;
+        while (cand) {
+          const int y = __ffs(cand) - 1;
+          cand &= cand - 1;
+          dirty &= ~(1u << y);
+          if (visit(y)) mine |= 1u << y;
+        }
+        __syncwarp();
+        // new neighbour columns; the damaged neighbours of every repair become dirty
+        const uint32_t ol = lm, orr = rm;
+        refresh();
+        const uint32_t gone = (ol & ~lm) | (orr & ~rm) | mine;
+        dirty |= (gone | (gone << 1) | (gone >> 1)) & own & live;
+        ++t;
+        // the window of step t + 1: one row further, and row 0 when t + 1 - 2x is 0 mod 4
+        win = (win << 1) | (((t - x2) & static_cast<int>(0x80000003u)) == 0 ? 1u : 0u);
+      } else {
+        t = next_step(t + 1);
+        win = window(t);
       }
-      __syncwarp();
-      // new neighbour columns; the damaged neighbours of every repair become dirty
-      const uint32_t ol = lm, orr = rm;
-      refresh();
-      const uint32_t gone = (ol & ~lm) | (orr & ~rm) | mine;
-      dirty |= (gone | (gone << 1) | (gone >> 1)) & own & rows;
     }
     // ---- repaired pixels back into the view, and the formatted outputs where it changed:
     // the anaglyph takes red from the left view and green, blue from the right one; a
