@@ -281,7 +281,7 @@ dibr_status dibr_synthesize_batch_static(int n, const dibr_image *imgs, const di
  *                  frame before it, its launch takes 1/n of the SM slots (in taller row
  *                  bands), so that n consecutive frames run side by side; 1: every launch
  *                  spreads over all SMs.  A launch on an idle stream always does.
- *                  Automatic: 8.
+ *                  Automatic: 7.
  * dibr_set_tuning() rejects out-of-range values with DIBR_E_INVALID. */
 typedef struct {
     int32_t ring_slots, ctas_per_sm, load_mode, l2_prefetch, rows_per_unit, host_bands;

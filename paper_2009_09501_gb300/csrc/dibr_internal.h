@@ -12,7 +12,7 @@ namespace dibr {
 
 constexpr int kChunk = 16;          // pixels owned by one consumer thread per pass
 constexpr int kMaxRing = 8;         // TMA row-ring slots at most
-constexpr int kFramesInFlight = 8;  // consecutive independent frames side by side (automatic)
+constexpr int kFramesInFlight = 7;  // consecutive independent frames side by side (automatic)
 constexpr int kBoxBytes = 256;      // 2-D TMA box width (bytes) for rows with 3*W not a multiple of 16
 constexpr int kMaxConsumers = 512;  // threads per CTA at most (8K rows use 480)
 constexpr int kMaxWidth = 7680;   // 8K UHD: the widest row whose z-buffers and ring fit on chip
