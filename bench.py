@@ -63,6 +63,7 @@ def whole_job_rate(units_per_rank, seconds_per_rank, world, dist=None, device="c
 
 BAND_SOURCES = ("dibr_band.cu", "dibr_internal.h", "dibr_ptx.cuh")
 INPAINT_SOURCES = ("dibr_inpaint.cu", "dibr_internal.h", "dibr_ptx.cuh")
+XBF_SOURCES = ("dibr_xbf.cu", "dibr_internal.h", "dibr_ptx.cuh")
 
 
 def kernel_source_digest(files=BAND_SOURCES):
@@ -415,6 +416,17 @@ def bench_xbf(D, torch, ctx, stream, reps=200):
     xbf_us = res["xbf"] - res["binom5"] + 0.0
     clock_hz = 2.07e9  # the maximum SM clock; the clocks sampled in the timed region bound it
     peak = 16 * props.multi_processor_count * clock_hz  # exp2 results per second (16 per SM per clock)
+    # the bound that holds: instruction issue (warp instructions per 4K frame, fixed for this
+    # workload and code, from the committed ncu summary; one per clock per scheduler)
+    ipeak = 4 * props.multi_processor_count * clock_hz
+    insts, isrc = load_profile_value("xbf_kernel_4k.md", "warp_instructions_per_launch", XBF_SOURCES)
+    issue = {"bound": "issue", "unit": "warp instructions/s", "peak": ipeak,
+             "peak_source": "4 schedulers x SMs x 2.07 GHz (derived)", "instructions_per_frame": insts,
+             "instructions_source": isrc,
+             "thread_instructions_per_tap": insts * 32 / taps if insts else None,
+             "floor_us": insts / ipeak * 1e6 if insts else None,
+             "achieved": insts / (xbf_us * 1e-6) if insts and xbf_us > 0 else None,
+             "frac": insts / (xbf_us * 1e-6) / ipeak if insts and xbf_us > 0 else None}
     return {"workload": "3840x2160, P=64, L+R+anaglyph, cross-bilateral depth r=2",
             "frames_per_s": 1e6 / res["xbf"], "us_per_frame": res["xbf"],
             "binom5_us_per_frame": res["binom5"], "xbf_kernel_us_est": xbf_us,
@@ -422,7 +434,8 @@ def bench_xbf(D, torch, ctx, stream, reps=200):
                          "achieved": taps / (xbf_us * 1e-6) if xbf_us > 0 else None, "peak": peak,
                          "frac": taps / (xbf_us * 1e-6) / peak if xbf_us > 0 else None,
                          "peak_source": "16 exp2/clock/SM x SMs x 2.07 GHz (derived)",
-                         "note": "kernel time estimated as the frame time with this depth rule minus the binomial one"}}
+                         "note": "kernel time estimated as the frame time with this depth rule minus the binomial one"},
+            "issue_roofline": issue}
 
 
 def bench_video(D, torch, ctx, frames=300):
