@@ -449,7 +449,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, unsign
 // processed before (each per-row mbarrier completes one phase per row); both are advanced
 // here.  Returns false when a bounded wait gave up (the status word is set and the copies
 // in flight have landed).
-template <int DS, bool FWD>
+// OUTS: the requested outputs when fixed at compile time (the stereo set, every output row
+// 16-byte aligned: whole chunks stored as 16-byte words), 0 when read from the arguments.
+template <int DS, bool FWD, uint32_t OUTS = 0>
 __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
                                          uint32_t &nrows, int *status,
                                          unsigned long long timeout_ns) {
@@ -522,7 +524,8 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   // the warp's 32 chunks are all whole (every warp of a row but possibly the last):
   // warp-uniform fast paths for its depth row, clears and stores
   const bool wfull = __all_sync(kAll, npx == kChunk);
-  const bool wfast = wfull && a.fast_store;
+  const bool fast_store = OUTS ? true : a.fast_store != 0;
+  const bool wfast = wfull && fast_store;
   const int x0c = min(x0, (a.nch - 1) * kChunk);  // clamped: loads stay inside the buffers
   const int warp_lo = (tid & ~31) * kChunk;
   const int warp_hi = min(W, warp_lo + 32 * kChunk);
@@ -538,12 +541,13 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
   // shared address of target 0 of the z-buffer row of parity p, view v
   auto zrow = [&](int p, int v) { return m.zb + 4u * static_cast<uint32_t>(m.zguard + (2 * p + v) * m.zstride); };
 
-  const bool want_depth = (a.outputs & DIBR_OUT_DEPTH) != 0;
-  const bool want_holes = (a.outputs & DIBR_OUT_HOLES) != 0;
-  const bool want_ana = (a.outputs & DIBR_OUT_ANAGLYPH) != 0;
-  const bool want_l = (a.outputs & DIBR_OUT_LEFT) != 0;
-  const bool want_r = (a.outputs & DIBR_OUT_RIGHT) != 0;
-  const bool want_hsbs = (a.outputs & DIBR_OUT_HSBS) != 0;
+  const uint32_t outs = OUTS ? OUTS : a.outputs;
+  const bool want_depth = (outs & DIBR_OUT_DEPTH) != 0;
+  const bool want_holes = (outs & DIBR_OUT_HOLES) != 0;
+  const bool want_ana = (outs & DIBR_OUT_ANAGLYPH) != 0;
+  const bool want_l = (outs & DIBR_OUT_LEFT) != 0;
+  const bool want_r = (outs & DIBR_OUT_RIGHT) != 0;
+  const bool want_hsbs = (outs & DIBR_OUT_HSBS) != 0;
 
   // every z-buffer target empty (later rows: C clears its targets once it has read them)
   if (FWD) {
@@ -687,7 +691,7 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     // side-by-side frame and, after the right view, the anaglyph (red from the left view,
     // green and blue from the right: in the packed words, the bytes at offsets 0 mod 3).
     const int64_t ro = static_cast<int64_t>(y) * a.out_pitch;
-    const bool fast = wfast || (a.fast_store && npx == kChunk);
+    const bool fast = wfast || (fast_store && npx == kChunk);
     uint32_t wl[12];
     auto emit_view = [&](int v, const uint32_t (&kv)[16]) {
       if (!wfull && !active) return;
@@ -916,7 +920,7 @@ __device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
 
 // ---------------------------------------------------------------------------------
 // One image: CTA b owns the rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0.
-template <int DS, bool FWD>
+template <int DS, bool FWD, uint32_t OUTS>
 __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
   // The next launch on the stream may start its set-up while this one runs (programmatic
   // dependent launch); it waits below for this one to complete before any global access.
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
     j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
     j.outputs = a.outputs; j.l2_prefetch = a.l2_prefetch; j.fast_store = a.fast_store;
     uint32_t kbase = 0, nrows = 0;
-    run_band<DS, FWD>(j, m, ys, ye, kbase, nrows, a.status, a.timeout_ns);
+    run_band<DS, FWD, OUTS>(j, m, ys, ye, kbase, nrows, a.status, a.timeout_ns);
   }
   if (a.overlap) griddep_wait();
 }
@@ -1029,10 +1033,10 @@ cudaError_t allow_smem(K kernel, std::atomic<uint64_t> &done) {
   return e;
 }
 
-template <int DS, bool FWD>
+template <int DS, bool FWD, uint32_t OUTS = 0>
 cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
   static std::atomic<uint64_t> done{0};
-  cudaError_t e = allow_smem(band_kernel<DS, FWD>, done);
+  cudaError_t e = allow_smem(band_kernel<DS, FWD, OUTS>, done);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.grid);
@@ -1044,7 +1048,7 @@ cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, band_kernel<DS, FWD>, a);
+  e = cudaLaunchKernelEx(&cfg, band_kernel<DS, FWD, OUTS>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1053,6 +1057,10 @@ cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
   (void)ctas_per_sm;
   const bool fwd = a.warp_mode == DIBR_WARP_FORWARD;
+  // the stereo set (left, right, anaglyph) with 16-byte aligned rows: its own instance
+  constexpr uint32_t kStereo = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT;
+  if (a.depth_src == DS_BINOM5 && fwd && a.outputs == kStereo && a.fast_store)
+    return launch_band_t<DS_BINOM5, true, kStereo>(a, smem_bytes, st);
   switch (a.depth_src) {
     case DS_BINOM5: return fwd ? launch_band_t<DS_BINOM5, true>(a, smem_bytes, st) : launch_band_t<DS_BINOM5, false>(a, smem_bytes, st);
     case DS_LUMA: return fwd ? launch_band_t<DS_LUMA, true>(a, smem_bytes, st) : launch_band_t<DS_LUMA, false>(a, smem_bytes, st);
