@@ -961,6 +961,9 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
 // ---------------------------------------------------------------------------------
 // A batch of images in one persistent launch: CTAs pull work units (an image and a
 // range of its rows) from a device counter until none is left.
+// OUTS: every image of the launch has this fixed output set (binomial depth, forward warp,
+// aligned rows); 0: each image's own choices.
+template <uint32_t OUTS>
 __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
   // The next launch of the batch (another group of images, independent of this one) may be
   // placed as soon as every CTA of this one runs: its CTAs take the SM slots this launch
@@ -999,12 +1002,13 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     j.outputs = dsc.outputs; j.l2_prefetch = 0;
     j.fast_store = ((reinterpret_cast<uintptr_t>(dsc.out[O_ANA]) | reinterpret_cast<uintptr_t>(dsc.out[O_LEFT]) |
                      reinterpret_cast<uintptr_t>(dsc.out[O_RIGHT]) | static_cast<uintptr_t>(dsc.out_pitch)) & 15u) == 0;
-    const bool fwd = dsc.warp_mode == DIBR_WARP_FORWARD;
+    const bool fwd = OUTS ? true : dsc.warp_mode == DIBR_WARP_FORWARD;
     if (fwd) fill_luts<true>(m, dsc.lut_h, dsc.lut_n);
     else fill_luts<false>(m, dsc.lut_h, dsc.lut_n);
     __syncthreads();
     bool ok;
-    switch (dsc.depth_src * 2 + (fwd ? 0 : 1)) {
+    if (OUTS) ok = run_band<DS_BINOM5, true, OUTS>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns);
+    else switch (dsc.depth_src * 2 + (fwd ? 0 : 1)) {
       case DS_BINOM5 * 2: ok = run_band<DS_BINOM5, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
       case DS_BINOM5 * 2 + 1: ok = run_band<DS_BINOM5, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
       case DS_LUMA * 2: ok = run_band<DS_LUMA, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
@@ -1057,10 +1061,12 @@ cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
 cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cudaStream_t st) {
   (void)ctas_per_sm;
   const bool fwd = a.warp_mode == DIBR_WARP_FORWARD;
-  // the stereo set (left, right, anaglyph) with 16-byte aligned rows: its own instance
-  constexpr uint32_t kStereo = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT;
-  if (a.depth_src == DS_BINOM5 && fwd && a.outputs == kStereo && a.fast_store)
-    return launch_band_t<DS_BINOM5, true, kStereo>(a, smem_bytes, st);
+  // the stereo set (left, right, anaglyph) and the anaglyph alone, with 16-byte aligned
+  // rows: instances of their own
+  if (a.depth_src == DS_BINOM5 && fwd && a.fast_store) {
+    if (a.outputs == kSetStereo) return launch_band_t<DS_BINOM5, true, kSetStereo>(a, smem_bytes, st);
+    if (a.outputs == kSetAnaglyph) return launch_band_t<DS_BINOM5, true, kSetAnaglyph>(a, smem_bytes, st);
+  }
   switch (a.depth_src) {
     case DS_BINOM5: return fwd ? launch_band_t<DS_BINOM5, true>(a, smem_bytes, st) : launch_band_t<DS_BINOM5, false>(a, smem_bytes, st);
     case DS_LUMA: return fwd ? launch_band_t<DS_LUMA, true>(a, smem_bytes, st) : launch_band_t<DS_LUMA, false>(a, smem_bytes, st);
@@ -1068,9 +1074,10 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
   }
 }
 
-cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {
+template <uint32_t OUTS>
+static cudaError_t launch_batch_t(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {
   static std::atomic<uint64_t> done{0};
-  cudaError_t e = allow_smem(batch_kernel, done);
+  cudaError_t e = allow_smem(batch_kernel<OUTS>, done);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1082,8 +1089,14 @@ cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chai
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
-  e = cudaLaunchKernelEx(&cfg, batch_kernel, b);
+  e = cudaLaunchKernelEx(&cfg, batch_kernel<OUTS>, b);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchArgs &b, int grid, int smem_bytes, bool chained, cudaStream_t st) {
+  if (b.outs == kSetStereo) return launch_batch_t<kSetStereo>(b, grid, smem_bytes, chained, st);
+  if (b.outs == kSetAnaglyph) return launch_batch_t<kSetAnaglyph>(b, grid, smem_bytes, chained, st);
+  return launch_batch_t<0>(b, grid, smem_bytes, chained, st);
 }
 
 }  // namespace dibr

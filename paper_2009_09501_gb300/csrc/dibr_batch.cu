@@ -238,6 +238,13 @@ dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_
     d.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : pp.depth_rule == DIBR_DEPTH_LUMA ? DS_LUMA : DS_GLOBAL;
     shift_tables(&pp, d.lut_h, d.lut_n);
   }
+  // every image of one fixed output set: the launches use that set's kernel instance
+  uint32_t fixed = 0;
+  for (int i = 0; i < n; ++i) {
+    const ImageDesc &d = descs[i];
+    const uint32_t f = fixed_set(d.outputs, d.depth_src, d.warp_mode, d.out, d.out_pitch);
+    fixed = i == 0 ? f : (f == fixed ? fixed : 0u);
+  }
   int u = 0;
   for (int c = 0; c < nclass; ++c) {
     cls[c].unit_begin = u;
@@ -266,6 +273,7 @@ dibr_status dibr_ctx::enqueue_grouped(int n, const dibr_image *imgs, const dibr_
     b.nch_max = cls[c].nch_max;
     b.nc = cls[c].nc;
     b.zguard = lim.zguard;
+    b.outs = fixed;
     const int grid = std::max(1, std::min(cls[c].n_units, num_sms * cls[c].per));
     e = launch_batch(b, grid, cls[c].smem, c > 0, stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");

@@ -162,7 +162,22 @@ struct BatchArgs {
   int *status;
   unsigned long long timeout_ns;
   int32_t nb, srow, nch_max, nc, zguard;
+  uint32_t outs;  // kSetStereo / kSetAnaglyph: every image is of that kind (fixed_set); 0: any
 };
+
+// Output sets with kernel instances of their own (outputs fixed at compile time): binomial
+// depth, forward warp, and every requested RGB output and the output pitch 16-byte aligned.
+constexpr uint32_t kSetStereo = DIBR_OUT_ANAGLYPH | DIBR_OUT_LEFT | DIBR_OUT_RIGHT;
+constexpr uint32_t kSetAnaglyph = DIBR_OUT_ANAGLYPH;
+
+// The fixed set an image belongs to (kSetStereo, kSetAnaglyph), else 0.
+inline uint32_t fixed_set(uint32_t outputs, int depth_src, int warp_mode, const uint8_t *const *out, int64_t pitch) {
+  if (depth_src != DS_BINOM5 || warp_mode != DIBR_WARP_FORWARD) return 0u;
+  if (outputs != kSetStereo && outputs != kSetAnaglyph) return 0u;
+  const uintptr_t bits = reinterpret_cast<uintptr_t>(out[O_ANA]) | reinterpret_cast<uintptr_t>(out[O_LEFT]) |
+                         reinterpret_cast<uintptr_t>(out[O_RIGHT]) | static_cast<uintptr_t>(pitch);
+  return (bits & 15u) == 0 ? outputs : 0u;
+}
 
 // ---- planning a batch (host; no allocation, so the no-allocation entry point shares it)
 //

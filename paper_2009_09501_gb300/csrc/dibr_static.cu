@@ -169,6 +169,13 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     dd.depth_src = pp.depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
     shift_tables(&pp, dd.lut_h, dd.lut_n);
   }
+  // every image of one fixed output set: the launches use that set's kernel instance
+  uint32_t fixed = 0;
+  for (int i = 0; i < n; ++i) {
+    const uint32_t f = fixed_set(descs[i].outputs, descs[i].depth_src, descs[i].warp_mode, descs[i].out,
+                                 descs[i].out_pitch);
+    fixed = i == 0 ? f : (f == fixed ? fixed : 0u);
+  }
   int n_units = 0;
   for (int c = 0; c < nclass; ++c) {
     cls[c].unit_begin = n_units;
@@ -199,6 +206,7 @@ extern "C" dibr_status dibr_synthesize_batch_static(int n, const dibr_image *img
     b.nch_max = cls[c].nch_max;
     b.nc = cls[c].nc;
     b.zguard = zguard;
+    b.outs = fixed;
     const int grid = cls[c].n_units < d.sms * cls[c].per ? cls[c].n_units : d.sms * cls[c].per;
     e = launch_batch(b, grid > 0 ? grid : 1, cls[c].smem, c > 0, stream);
     if (e != cudaSuccess) return DIBR_E_CUDA;
