@@ -195,6 +195,26 @@ __device__ __forceinline__ void binom_h(const uint32_t (&Y)[10], uint32_t (&h)[8
 struct VCascade {
   uint32_t p0[8], p1[8], p2[8], p3[8];
 
+  // the state as 32 words (kept in tensor memory between rows by the fixed-set instances)
+  __device__ __forceinline__ void get(uint32_t (&t)[32]) const {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      t[i] = p0[i];
+      t[8 + i] = p1[i];
+      t[16 + i] = p2[i];
+      t[24 + i] = p3[i];
+    }
+  }
+  __device__ __forceinline__ void set(const uint32_t (&t)[32]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      p0[i] = t[i];
+      p1[i] = t[8 + i];
+      p2[i] = t[16 + i];
+      p3[i] = t[24 + i];
+    }
+  }
+
   __device__ __forceinline__ void clear() {
 #pragma unroll
     for (int i = 0; i < 8; ++i) p0[i] = p1[i] = p2[i] = p3[i] = 0u;
@@ -451,10 +471,13 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, unsign
 // in flight have landed).
 // OUTS: the requested outputs when fixed at compile time (the stereo set, every output row
 // 16-byte aligned: whole chunks stored as 16-byte words), 0 when read from the arguments.
-template <int DS, bool FWD, uint32_t OUTS = 0>
+//
+// TM: the vertical cascade's 32 words wait in tensor memory (at tmem, this thread's lane)
+// between one row's A and the next, so that B and C have those registers.
+template <int DS, bool FWD, uint32_t OUTS = 0, bool TM = false>
 __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int ye, uint32_t &kbase,
                                          uint32_t &nrows, int *status,
-                                         unsigned long long timeout_ns) {
+                                         unsigned long long timeout_ns, uint32_t tmem = 0u) {
   constexpr bool binom = DS == DS_BINOM5;
   const int tid = threadIdx.x, nc = blockDim.x, W = a.W, H = a.H, nb = m.nb;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nc >> 5;
@@ -570,6 +593,11 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
       binom_h(yq, hq);
       vc.feed(hq, V);
     }
+    if (TM) {
+      uint32_t t[32];
+      vc.get(t);
+      tmem_store32(tmem, t);
+    }
   }
   // the cleared z-buffers (and, with the binomial, the rows above the band) are done with
   bool aborted = consumer_sync_or(timed_out, nc);
@@ -590,15 +618,29 @@ __device__ __forceinline__ bool run_band(const Job &a, const Shm &m, int ys, int
     uint4 d;
     if (binom) {
       const int r2 = y + 2;
+      uint32_t t[32];
+      if (TM) tmem_load32(tmem, t);  // the cascade back (waited for just before it is fed)
       if (r2 < lb) wait_row(r2);
       uint32_t V[8];
       if (r2 < H) {
         uint32_t yq[10], hq[8];
         luma20(slot(r2), x0c, W, yq);
         binom_h(yq, hq);
+        if (TM) {
+          tmem_load_wait32(t);
+          vc.set(t);
+        }
         vc.feed(hq, V);
       } else {
+        if (TM) {
+          tmem_load_wait32(t);
+          vc.set(t);
+        }
         vc.feed_repeat(V);  // rows below the image repeat row H-1
+      }
+      if (TM) {
+        vc.get(t);
+        tmem_store32(tmem, t);
       }
       d = round_depth(V);
     } else if (DS == DS_LUMA) {
@@ -922,6 +964,8 @@ __device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
 // One image: CTA b owns the rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0.
 template <int DS, bool FWD, uint32_t OUTS>
 __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
+  // the fixed-set instances keep the binomial cascade in tensor memory between rows
+  constexpr bool TM = OUTS != 0 && DS == DS_BINOM5;
   // The next launch on the stream may start its set-up while this one runs (programmatic
   // dependent launch); it waits below for this one to complete before any global access.
   griddep_launch_dependents();
@@ -953,7 +997,28 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_con
     j.nbox = a.nbox; j.box_bytes = a.box_bytes; j.box_step = a.box_step;
     j.outputs = a.outputs; j.l2_prefetch = a.l2_prefetch; j.fast_store = a.fast_store;
     uint32_t kbase = 0, nrows = 0;
-    run_band<DS, FWD, OUTS>(j, m, ys, ye, kbase, nrows, a.status, a.timeout_ns);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // 32 columns per group of four warps (a warp reaches only its quarter of the lanes),
+    // rounded up to a power of two: at most 128 of the SM's 512 columns per CTA, and
+    // 512 / 128 = 4 CTAs of 16 warps would not fit an SM's 2048 threads anyway
+    const uint32_t ncols = nwarps <= 4 ? 32u : nwarps <= 8 ? 64u : 128u;
+    uint32_t tbase = 0u;
+    if (TM) {
+      const uint32_t slot_addr = smem_addr(smem + band_smem_layout(a.nb, a.srow, a.nch, nwarps, a.zguard).flags + 48);
+      if (warp == 0) tmem_alloc(slot_addr, ncols);
+      tmem_fence_before_sync();
+      __syncthreads();
+      tmem_fence_after_sync();
+      tbase = lds_u32(slot_addr);
+    }
+    const uint32_t tmem = tbase + ((32u * (warp & 3)) << 16) + 32u * (warp >> 2);
+    run_band<DS, FWD, OUTS, TM>(j, m, ys, ye, kbase, nrows, a.status, a.timeout_ns, tmem);
+    if (TM) {  // every thread's stores have completed (each store waits for itself)
+      tmem_fence_before_sync();
+      __syncthreads();
+      tmem_fence_after_sync();
+      if (warp == 0) tmem_dealloc(tbase, ncols);
+    }
   }
   if (a.overlap) griddep_wait();
 }
