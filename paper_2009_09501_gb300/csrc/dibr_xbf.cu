@@ -7,22 +7,23 @@
 // Y(p) (sum w (Y(q) - Y(p))), which is the same quotient and keeps the rounding error of
 // the accumulation small next to the final half-integer decision.
 //
-// One CTA computes a 32 x 8 tile; the tile plus an r-pixel apron is staged in shared
-// memory once, one 8-byte cell per pixel: the colour (RGB in the low three bytes) and the
+// One CTA computes a 32 x 16 tile (two vertically adjacent pixels per thread); the tile plus
+// an r-pixel apron is staged in shared memory once, one 8-byte cell per pixel: the colour (RGB in the low three bytes) and the
 // luminance (as a float).  Per tap: one shared load, the squared colour distance exactly
 // in two integer instructions (per-byte absolute differences, then a byte dot product of
 // that word with itself), one FMA for the exponent (the spatial part is a per-tap
 // constant: the radius is a template parameter, so the taps unroll), one exp2 on the
-// special-function unit (the constants are pre-scaled by log2 e), and two accumulations.  The integer-to-float conversion of the distance, which would share
-// the special-function unit's low rate, is an exact mantissa trick, so the exp2 is the
-// only such operation per tap.
+// special-function unit (the constants are pre-scaled by log2 e), and two accumulations.
+// The distance's integer-to-float conversion shares the special-function unit's rate: the
+// kernel is bound by instruction issue, not by that unit, and the conversion takes one issue
+// slot where an exact mantissa trick (OR into 2^23, subtract 2^23) takes two.
 #include "dibr_internal.h"
 #include "dibr_ptx.cuh"
 
 namespace dibr {
 namespace {
 
-constexpr int kTX = 32, kTY = 8;  // tile; radius 1..8 (template parameter)
+constexpr int kTX = 32, kTY = 8;  // threads per CTA: kTX x kTY; tiles of kTX x 2 kTY pixels; radius 1..8
 
 __device__ __forceinline__ uint32_t luma8x(uint32_t r, uint32_t g, uint32_t b) {
   return (299u * r + 587u * g + 114u * b + 500u) / 1000u;
@@ -35,29 +36,53 @@ __device__ __forceinline__ float ex2(float x) {
   return y;
 }
 
-// Integers below 2^23 become floats without the conversion unit: OR-ed into the mantissa of
-// 2^23 (bit pattern 0x4B000000), minus 2^23, exactly.
-constexpr float kTwo23 = 8388608.0f;
-
 // One tap: q's colour cq and luminance yq against the centre's colour cp and luminance yp;
 // es = -(dx^2+dy^2) as log2(e).
 __device__ __forceinline__ void xbf_tap(uint32_t cp, uint32_t cq, float yq, float es, float nar, float yp, float &num,
                                         float &den) {
   const uint32_t v = __vabsdiffu4(cp, cq);
   const uint32_t d2 = __dp4a(v, v, 0u);  // |RGB(p) - RGB(q)|^2, exact, < 2^18
-  const float fd2 = __uint_as_float(0x4B000000u | d2) - kTwo23;
+  const float fd2 = __uint2float_rn(d2);  // exact (d2 < 2^24)
   const float w = ex2(fmaf(fd2, nar, es));
   num = fmaf(w, yq - yp, num);
   den += w;
 }
 
+// The depth of one pixel from the staged tile, window clipped to the image (cell (cy, cx) of
+// the tile holds the pixel itself).
+template <int R>
+__device__ __forceinline__ float xbf_clipped(const uint2 (*px)[kTX + 2 * R], int cy, int cx, int x, int y, int W, int H,
+                                             float nas, float nar, float &yp_out) {
+  const uint2 pc = px[cy][cx];
+  const float yp = __uint_as_float(pc.y);
+  float num = 0.f, den = 0.f;
+  const int x0 = max(-R, -x), x1 = min(R, W - 1 - x), y0 = max(-R, -y), y1 = min(R, H - 1 - y);
+  for (int dy = y0; dy <= y1; ++dy)
+    for (int dx = x0; dx <= x1; ++dx) {
+      const uint2 q = px[cy + dy][cx + dx];
+      xbf_tap(pc.x, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+    }
+  yp_out = yp;
+  return num / den;
+}
+
+__device__ __forceinline__ void xbf_store(uint8_t *D, int64_t dpitch, int x, int y, float yp, float rel) {
+  const float q = floorf(rel + 0.5f);
+  const int v = static_cast<int>(yp) + static_cast<int>(q);
+  D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
+}
+
+// One CTA: a 32 x 16 tile, each thread the two vertically adjacent pixels (x, y0) and
+// (x, y0 + 1), whose windows share 2R of their 2R + 1 rows: a cell of those rows is loaded
+// once for both.
 template <int R>
 __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
                                                        float as, float ar, uint8_t *__restrict__ D, int64_t dpitch,
                                                        int after) {
-  __shared__ uint2 px[kTY + 2 * R][kTX + 2 * R];  // colour 0x00BBGGRR, luminance as float bits
-  const int bx = blockIdx.x * kTX, by = blockIdx.y * kTY;
-  constexpr int ax = kTX + 2 * R, ay = kTY + 2 * R;
+  constexpr int kRows = 2 * kTY;  // tile rows
+  __shared__ uint2 px[kRows + 2 * R][kTX + 2 * R];  // colour 0x00BBGGRR, luminance as float bits
+  const int bx = blockIdx.x * kTX, by = blockIdx.y * kRows;
+  constexpr int ax = kTX + 2 * R, ay = kRows + 2 * R;
   for (int i = threadIdx.x; i < ax * ay; i += blockDim.x) {
     const int ty = i / ax, tx = i - ty * ax;
     const int gx = bx - R + tx, gy = by - R + ty;
@@ -72,38 +97,42 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
     px[ty][tx] = make_uint2(c, __float_as_uint(static_cast<float>(l)));
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  const int tx = threadIdx.x % kTX, ty = 2 * (threadIdx.x / kTX);
   const int x = bx + tx, y = by + ty;
   if (x >= W || y >= H) {
     if (after) griddep_wait();
     return;
   }
-  const uint2 pc = px[ty + R][tx + R];
-  const uint32_t cp = pc.x;
-  const float yp = __uint_as_float(pc.y);
   // exponents in base 2: w = 2^(-(s2 * as + d2 * ar) * log2 e)
   constexpr float kLog2e = 1.4426950408889634f;
   const float nas = -as * kLog2e, nar = -ar * kLog2e;
-  float num = 0.f, den = 0.f;
-  if (x >= R && x + R < W && y >= R && y + R < H) {
+  const bool second = y + 1 < H;
+  if (x >= R && x + R < W && y >= R && y + 1 + R < H) {
+    const uint2 pa = px[ty + R][tx + R], pb = px[ty + 1 + R][tx + R];
+    const float ya = __uint_as_float(pa.y), yb = __uint_as_float(pb.y);
+    float na = 0.f, da = 0.f, nb = 0.f, db = 0.f;
 #pragma unroll
-    for (int dy = -R; dy <= R; ++dy)
+    for (int dy = -R; dy <= R + 1; ++dy)
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx) {
         const uint2 q = px[ty + R + dy][tx + R + dx];
-        xbf_tap(cp, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
+        if (dy <= R)
+          xbf_tap(pa.x, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, ya, na, da);
+        if (dy >= 1 - R)
+          xbf_tap(pb.x, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + (dy - 1) * (dy - 1)) * nas, nar, yb,
+                  nb, db);
       }
-  } else {  // the window clipped to the image
-    const int x0 = max(-R, -x), x1 = min(R, W - 1 - x), y0 = max(-R, -y), y1 = min(R, H - 1 - y);
-    for (int dy = y0; dy <= y1; ++dy)
-      for (int dx = x0; dx <= x1; ++dx) {
-        const uint2 q = px[ty + R + dy][tx + R + dx];
-        xbf_tap(cp, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, yp, num, den);
-      }
+    xbf_store(D, dpitch, x, y, ya, na / da);
+    xbf_store(D, dpitch, x, y + 1, yb, nb / db);
+  } else {  // a window clipped to the image
+    float yp;
+    const float ra = xbf_clipped<R>(px, ty + R, tx + R, x, y, W, H, nas, nar, yp);
+    xbf_store(D, dpitch, x, y, yp, ra);
+    if (second) {
+      const float rb = xbf_clipped<R>(px, ty + 1 + R, tx + R, x, y + 1, W, H, nas, nar, yp);
+      xbf_store(D, dpitch, x, y + 1, yp, rb);
+    }
   }
-  const float q = floorf(num / den + 0.5f);
-  const int v = static_cast<int>(yp) + static_cast<int>(q);
-  D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
   // launched to run beside the previous launch on the stream (whose buffers the host found
   // disjoint from this one's): complete only after it, so that the stream order holds
   if (after) griddep_wait();
@@ -113,7 +142,7 @@ template <int R>
 cudaError_t launch_r(const uint8_t *rgb, int64_t pitch, int W, int H, float as, float ar, uint8_t *D, int64_t dpitch,
                      cudaStream_t st, bool after) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((W + kTX - 1) / kTX, (H + kTY - 1) / kTY);
+  cfg.gridDim = dim3((W + kTX - 1) / kTX, (H + 2 * kTY - 1) / (2 * kTY));
   cfg.blockDim = dim3(kTX * kTY);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
