@@ -23,7 +23,8 @@
 namespace dibr {
 namespace {
 
-constexpr int kTX = 32, kTY = 8;  // threads per CTA: kTX x kTY; tiles of kTX x 2 kTY pixels; radius 1..8
+constexpr int kTX = 32, kTY = 8;  // threads per CTA: kTX x kTY; tiles of kTX x kPY kTY pixels; radius 1..8
+constexpr int kPY = 4;             // pixels per thread, vertically adjacent
 
 __device__ __forceinline__ uint32_t luma8x(uint32_t r, uint32_t g, uint32_t b) {
   return (299u * r + 587u * g + 114u * b + 500u) / 1000u;
@@ -72,14 +73,14 @@ __device__ __forceinline__ void xbf_store(uint8_t *D, int64_t dpitch, int x, int
   D[static_cast<int64_t>(y) * dpitch + x] = static_cast<uint8_t>(min(max(v, 0), 255));
 }
 
-// One CTA: a 32 x 16 tile, each thread the two vertically adjacent pixels (x, y0) and
-// (x, y0 + 1), whose windows share 2R of their 2R + 1 rows: a cell of those rows is loaded
-// once for both.
+// One CTA: a 32 x (8 kPY) tile, each thread kPY vertically adjacent pixels (x, y0 + i),
+// whose windows share rows: a cell of the 2R + kPY rows they span is loaded once for all of
+// the pixels whose window holds it.
 template <int R>
 __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict__ rgb, int64_t pitch, int W, int H,
                                                        float as, float ar, uint8_t *__restrict__ D, int64_t dpitch,
                                                        int after) {
-  constexpr int kRows = 2 * kTY;  // tile rows
+  constexpr int kRows = kPY * kTY;  // tile rows
   __shared__ uint2 px[kRows + 2 * R][kTX + 2 * R];  // colour 0x00BBGGRR, luminance as float bits
   const int bx = blockIdx.x * kTX, by = blockIdx.y * kRows;
   constexpr int ax = kTX + 2 * R, ay = kRows + 2 * R;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
     px[ty][tx] = make_uint2(c, __float_as_uint(static_cast<float>(l)));
   }
   __syncthreads();
-  const int tx = threadIdx.x % kTX, ty = 2 * (threadIdx.x / kTX);
+  const int tx = threadIdx.x % kTX, ty = kPY * (threadIdx.x / kTX);
   const int x = bx + tx, y = by + ty;
   if (x >= W || y >= H) {
     if (after) griddep_wait();
@@ -106,31 +107,34 @@ __global__ void __launch_bounds__(kTX *kTY) xbf_kernel(const uint8_t *__restrict
   // exponents in base 2: w = 2^(-(s2 * as + d2 * ar) * log2 e)
   constexpr float kLog2e = 1.4426950408889634f;
   const float nas = -as * kLog2e, nar = -ar * kLog2e;
-  const bool second = y + 1 < H;
-  if (x >= R && x + R < W && y >= R && y + 1 + R < H) {
-    const uint2 pa = px[ty + R][tx + R], pb = px[ty + 1 + R][tx + R];
-    const float ya = __uint_as_float(pa.y), yb = __uint_as_float(pb.y);
-    float na = 0.f, da = 0.f, nb = 0.f, db = 0.f;
+  if (x >= R && x + R < W && y >= R && y + kPY - 1 + R < H) {
+    uint32_t cp[kPY];
+    float yp[kPY], num[kPY], den[kPY];
 #pragma unroll
-    for (int dy = -R; dy <= R + 1; ++dy)
+    for (int i = 0; i < kPY; ++i) {
+      const uint2 pc = px[ty + i + R][tx + R];
+      cp[i] = pc.x;
+      yp[i] = __uint_as_float(pc.y);
+      num[i] = den[i] = 0.f;
+    }
+#pragma unroll
+    for (int dy = -R; dy <= R + kPY - 1; ++dy)
 #pragma unroll
       for (int dx = -R; dx <= R; ++dx) {
         const uint2 q = px[ty + R + dy][tx + R + dx];
-        if (dy <= R)
-          xbf_tap(pa.x, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + dy * dy) * nas, nar, ya, na, da);
-        if (dy >= 1 - R)
-          xbf_tap(pb.x, q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + (dy - 1) * (dy - 1)) * nas, nar, yb,
-                  nb, db);
+#pragma unroll
+        for (int i = 0; i < kPY; ++i)
+          if (dy - i >= -R && dy - i <= R)  // row dy of pixel i's window (compile time)
+            xbf_tap(cp[i], q.x, __uint_as_float(q.y), static_cast<float>(dx * dx + (dy - i) * (dy - i)) * nas, nar,
+                    yp[i], num[i], den[i]);
       }
-    xbf_store(D, dpitch, x, y, ya, na / da);
-    xbf_store(D, dpitch, x, y + 1, yb, nb / db);
+#pragma unroll
+    for (int i = 0; i < kPY; ++i) xbf_store(D, dpitch, x, y + i, yp[i], num[i] / den[i]);
   } else {  // a window clipped to the image
-    float yp;
-    const float ra = xbf_clipped<R>(px, ty + R, tx + R, x, y, W, H, nas, nar, yp);
-    xbf_store(D, dpitch, x, y, yp, ra);
-    if (second) {
-      const float rb = xbf_clipped<R>(px, ty + 1 + R, tx + R, x, y + 1, W, H, nas, nar, yp);
-      xbf_store(D, dpitch, x, y + 1, yp, rb);
+    for (int i = 0; i < kPY && y + i < H; ++i) {
+      float yp;
+      const float r = xbf_clipped<R>(px, ty + i + R, tx + R, x, y + i, W, H, nas, nar, yp);
+      xbf_store(D, dpitch, x, y + i, yp, r);
     }
   }
   // launched to run beside the previous launch on the stream (whose buffers the host found
@@ -142,7 +146,7 @@ template <int R>
 cudaError_t launch_r(const uint8_t *rgb, int64_t pitch, int W, int H, float as, float ar, uint8_t *D, int64_t dpitch,
                      cudaStream_t st, bool after) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((W + kTX - 1) / kTX, (H + 2 * kTY - 1) / (2 * kTY));
+  cfg.gridDim = dim3((W + kTX - 1) / kTX, (H + kPY * kTY - 1) / (kPY * kTY));
   cfg.blockDim = dim3(kTX * kTY);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
