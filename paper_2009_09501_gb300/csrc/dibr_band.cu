@@ -43,6 +43,7 @@ namespace dibr {
 namespace {
 
 constexpr uint32_t kAll = 0xFFFFFFFFu;
+constexpr int kTmemMinRows = 8;  // rows per CTA from which the fixed-set instances use tensor memory
 
 // The wait for a CTA's own copies in flight before it exits after a failed wait: always the
 // full 2 s, whatever limit the other waits have, so that no copy lands in shared memory
@@ -962,10 +963,11 @@ __device__ __forceinline__ void init_barriers(const Shm &m, int nb) {
 
 // ---------------------------------------------------------------------------------
 // One image: CTA b owns the rows row0 + [b*n/grid, (b+1)*n/grid), n = row1 - row0.
-template <int DS, bool FWD, uint32_t OUTS>
+// TM (fixed-set instances with the binomial depth, bands of kTmemMinRows rows or more): the
+// cascade waits in tensor memory between rows.
+template <int DS, bool FWD, uint32_t OUTS, bool TM>
 __global__ void __launch_bounds__(kMaxConsumers, 1) band_kernel(const __grid_constant__ BandArgs a) {
-  // the fixed-set instances keep the binomial cascade in tensor memory between rows
-  constexpr bool TM = OUTS != 0 && DS == DS_BINOM5;
+  static_assert(!TM || (OUTS != 0 && DS == DS_BINOM5), "tensor memory only in the fixed-set binomial instances");
   // The next launch on the stream may start its set-up while this one runs (programmatic
   // dependent launch); it waits below for this one to complete before any global access.
   griddep_launch_dependents();
@@ -1102,10 +1104,10 @@ cudaError_t allow_smem(K kernel, std::atomic<uint64_t> &done) {
   return e;
 }
 
-template <int DS, bool FWD, uint32_t OUTS = 0>
+template <int DS, bool FWD, uint32_t OUTS = 0, bool TM = false>
 cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
   static std::atomic<uint64_t> done{0};
-  cudaError_t e = allow_smem(band_kernel<DS, FWD, OUTS>, done);
+  cudaError_t e = allow_smem(band_kernel<DS, FWD, OUTS, TM>, done);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.grid);
@@ -1117,7 +1119,7 @@ cudaError_t launch_band_t(const BandArgs &a, int smem_bytes, cudaStream_t st) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, band_kernel<DS, FWD, OUTS>, a);
+  e = cudaLaunchKernelEx(&cfg, band_kernel<DS, FWD, OUTS, TM>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -1129,8 +1131,14 @@ cudaError_t launch_band(const BandArgs &a, int smem_bytes, int ctas_per_sm, cuda
   // the stereo set (left, right, anaglyph) and the anaglyph alone, with 16-byte aligned
   // rows: instances of their own
   if (a.depth_src == DS_BINOM5 && fwd && a.fast_store) {
-    if (a.outputs == kSetStereo) return launch_band_t<DS_BINOM5, true, kSetStereo>(a, smem_bytes, st);
-    if (a.outputs == kSetAnaglyph) return launch_band_t<DS_BINOM5, true, kSetAnaglyph>(a, smem_bytes, st);
+    // bands of a few rows do not repay a CTA's tensor-memory allocation
+    const bool tm = a.row1 - a.row0 >= kTmemMinRows * a.grid;
+    if (a.outputs == kSetStereo)
+      return tm ? launch_band_t<DS_BINOM5, true, kSetStereo, true>(a, smem_bytes, st)
+                : launch_band_t<DS_BINOM5, true, kSetStereo, false>(a, smem_bytes, st);
+    if (a.outputs == kSetAnaglyph)
+      return tm ? launch_band_t<DS_BINOM5, true, kSetAnaglyph, true>(a, smem_bytes, st)
+                : launch_band_t<DS_BINOM5, true, kSetAnaglyph, false>(a, smem_bytes, st);
   }
   switch (a.depth_src) {
     case DS_BINOM5: return fwd ? launch_band_t<DS_BINOM5, true>(a, smem_bytes, st) : launch_band_t<DS_BINOM5, false>(a, smem_bytes, st);
