@@ -420,3 +420,20 @@ def test_4k_frames_side_by_side(ctx, torch, oracle, fif):
         ctx.set_tuning(frames_in_flight=0)
     for k in range(12):
         assert_same({n: v.cpu().numpy() for n, v in outs[k].items()}, refs[k % 2], "frame %d" % k)
+
+
+@pytest.mark.parametrize("W,H", [(2000, 1300), (1008, 2000), (3840, 2160), (2048, 1216)])
+@pytest.mark.parametrize("outputs", [("anaglyph", "left", "right"), ("anaglyph",)])
+def test_fixed_set_instances_in_tall_bands(ctx, torch, oracle, W, H, outputs):
+    # 16-byte aligned device rows (3W a multiple of 16) and one CTA per SM: bands of 8 or
+    # more rows, so the stereo / anaglyph instances that keep the vertical filter's state in
+    # tensor memory run (including rows whose last warp is partial)
+    img = scenes.Scene(W, H, seed=700 + W + H, n_objects=25).frame(0)
+    P = max(2, int(round(0.025 * W)))
+    ref = oracle.dibr_parallel(img, oracle_params(oracle, max_parallax=P), want=outputs)
+    ctx.set_tuning(ctas_per_sm=1)
+    try:
+        got = run_device(ctx, torch, img, outputs, max_parallax=P)
+    finally:
+        ctx.set_tuning(ctas_per_sm=0)
+    assert_same(got, ref, "%dx%d" % (W, H))
