@@ -1040,8 +1040,24 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
   const int nwarps = blockDim.x >> 5;
   // the barriers and the unit word sit at the same place in every image's layout
   const Shm m0 = carve(smem, b.nb, b.srow, b.nch_max, nwarps, b.zguard);
-  int *unit_s = reinterpret_cast<int *>(smem + band_smem_layout(b.nb, b.srow, b.nch_max, nwarps, b.zguard).flags);
+  const int flags = band_smem_layout(b.nb, b.srow, b.nch_max, nwarps, b.zguard).flags;
+  int *unit_s = reinterpret_cast<int *>(smem + flags);
   init_barriers(m0, b.nb);
+  // a fixed-set batch keeps each unit's binomial cascade in tensor memory between rows
+  // (allocated once per CTA, as in the band kernel)
+  constexpr bool TM = OUTS != 0;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t ncols = nwarps <= 4 ? 32u : nwarps <= 8 ? 64u : 128u;
+  const uint32_t tslot = smem_addr(smem + flags + 48);
+  uint32_t tbase = 0u;
+  if (TM) {
+    if (warp == 0) tmem_alloc(tslot, ncols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    tbase = lds_u32(tslot);
+  }
+  const uint32_t tmem = tbase + ((32u * (warp & 3)) << 16) + 32u * (warp >> 2);
   uint32_t kbase = 0, nrows = 0;
   while (true) {
     __syncthreads();  // the previous unit is done with the ring, tables and unit_s
@@ -1074,7 +1090,7 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
     else fill_luts<false>(m, dsc.lut_h, dsc.lut_n);
     __syncthreads();
     bool ok;
-    if (OUTS) ok = run_band<DS_BINOM5, true, OUTS>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns);
+    if (OUTS) ok = run_band<DS_BINOM5, true, OUTS, TM>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns, tmem);
     else switch (dsc.depth_src * 2 + (fwd ? 0 : 1)) {
       case DS_BINOM5 * 2: ok = run_band<DS_BINOM5, true>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
       case DS_BINOM5 * 2 + 1: ok = run_band<DS_BINOM5, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
@@ -1084,6 +1100,12 @@ __global__ void __launch_bounds__(kMaxConsumers, 1) batch_kernel(BatchArgs b) {
       default: ok = run_band<DS_GLOBAL, false>(j, m, un.y, un.z, kbase, nrows, b.status, b.timeout_ns); break;
     }
     if (!ok) break;
+  }
+  if (TM) {  // every thread's stores have completed (each store waits for itself)
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_dealloc(tbase, ncols);
   }
   // A chained launch's CTAs wait for the previous launch to complete before they exit, so
   // that the work after the batch in stream order still follows all of it.
