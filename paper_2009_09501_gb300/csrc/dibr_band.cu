@@ -33,6 +33,13 @@
 // barriers come in pairs used by alternate rows.  Every wait is bounded (%globaltimer); a
 // wait that gives up sets a bit of the status word and the CTA unwinds after letting its
 // own copies land.
+//
+// Instances: the requested outputs are read from the arguments, or fixed at compile time for
+// the two sets the workloads use (left + right + anaglyph, anaglyph alone; binomial depth,
+// forward warp, 16-byte aligned rows), which drops the output branches and the state they
+// keep live.  The fixed-set instances in bands of kTmemMinRows rows or more keep the vertical
+// cascade's 32 words per thread in tensor memory between one row's A and the next, so that B
+// and C have those registers.
 #include <atomic>
 
 #include "dibr.h"
