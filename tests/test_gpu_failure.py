@@ -6,6 +6,9 @@
   that would have succeeded a few microseconds later then give up, the launch unwinds
   after its own copies in flight have landed, and the call reports DIBR_E_TIMEOUT.  With
   the default limit restored, the same context -- and a served stream -- succeed again.
+- The same through the instances that keep the vertical filter's state in tensor memory
+  (a band launch in tall bands, a persistent batched launch): the unwinding releases the
+  tensor memory, and the context then produces exact frames.
 - A slow consumer: frames submitted while nobody polls complete and wait in the
   completion queue; submissions beyond a stream's slots and queue are refused with
   DIBR_E_BUSY, never dropped.
@@ -143,3 +146,38 @@ def test_slow_consumer_frames_wait_in_the_completion_queue(torch, oracle):
         assert ctx.poll(8, 1000) == []  # nothing else completes
         for s in sids:
             ctx.close_stream(s)
+
+
+def test_wait_limit_in_the_tensor_memory_instances(torch, oracle):
+    # the fixed-set instances that keep the vertical filter's state in tensor memory: a band
+    # launch in 14-row bands (one CTA per SM) and a persistent batched launch of 1080p frames;
+    # a wait that gives up must unwind through the release of the tensor memory, and the
+    # context must produce exact frames afterwards
+    img4k = scenes.config_scene(2)
+    p4k = D.make_params(max_parallax=64, outputs=("anaglyph",))
+    ref4k = oracle.dibr_parallel(img4k, oracle.params(max_parallax=64), want=("anaglyph",))
+    hd = [_frame(1920, 1080, 50 + k) for k in range(6)]
+    phd = D.make_params(max_parallax=48, outputs=("anaglyph",))
+    refhd = [oracle.dibr_parallel(im, oracle.params(max_parallax=48), want=("anaglyph",))["anaglyph"] for im in hd]
+    t4k = torch.from_numpy(img4k).cuda()
+    thd = [torch.from_numpy(im).cuda() for im in hd]
+    with D.Context(device=0) as ctx:
+        # one CTA per SM: 14-row bands for the 4K frame; 16-row work units: the 1080p frames
+        # share the persistent batched launch instead of launches of their own
+        ctx.set_tuning(ctas_per_sm=1, rows_per_unit=16)
+        for attempt in range(2):
+            ctx.set_wait_limit(1)
+            with pytest.raises(D.DibrError) as e:
+                ctx.synthesize_image(t4k, p4k, {"anaglyph": torch.zeros_like(t4k)})
+            assert e.value.status == D.DIBR_E_TIMEOUT
+            with pytest.raises(D.DibrError) as e:
+                ctx.synthesize_batch(thd, [phd] * len(thd), [{"anaglyph": torch.zeros_like(t)} for t in thd])
+            assert e.value.status == D.DIBR_E_TIMEOUT
+            ctx.set_wait_limit(0)
+            out = {"anaglyph": torch.zeros_like(t4k)}
+            ctx.synthesize_image(t4k, p4k, out)
+            assert np.array_equal(out["anaglyph"].cpu().numpy(), ref4k["anaglyph"]), attempt
+            outs = [{"anaglyph": torch.zeros_like(t)} for t in thd]
+            ctx.synthesize_batch(thd, [phd] * len(thd), outs)
+            for k, o in enumerate(outs):
+                assert np.array_equal(o["anaglyph"].cpu().numpy(), refhd[k]), (attempt, k)
