@@ -4,7 +4,9 @@
 Workload: one 3840 x 2160 RGB uint8 frame (seeded synthetic scene, 40 objects, sigma-8
 texture), maximum parallax 64 px, binomial depth smoothing, Fig. 3 shift rule, outputs
 left + right views and the red-cyan anaglyph.  A step is one pass of the whole pipeline
-over one frame: one launch of the fused kernel.
+over one frame: one launch of the fused kernel.  The steps are enqueued back to back on the
+library's stream with rotating buffers, so consecutive frames run side by side (each on a
+share of the SMs, in tall row bands); single launches on an idle GPU are timed apart.
 
 Prints one JSON line (rank 0):
   value      frames/s over all ranks, inputs resident in HBM, CUDA events on the
@@ -13,8 +15,10 @@ Prints one JSON line (rank 0):
              with pinned HOST input and outputs (every frame's H2D copy, kernels and D2H
              copies inside the timed region, three frames in flight), beside the blocking
              dibr_synthesize_image figure (blocking_call_value);
-  roofline   the fused kernel's algorithmic bytes per launch / its mean launch time
-             against the measured HBM copy bandwidth;
+  roofline   the fused kernel's algorithmic bytes per launch / its mean launch time (the
+             timed region's length / the launches in it) against the measured HBM copy
+             bandwidth, with the DRAM bytes of one steady-state launch from the committed
+             ncu summary;
   cpu_baseline  the CPU oracle on this host's cores (band-parallel over row bands), on a
              bounded sample of frames;
   clocks     SM clock samples taken by nvidia-smi during the timed region.
