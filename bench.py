@@ -21,7 +21,12 @@ Prints one JSON line (rank 0):
              ncu summary;
   cpu_baseline  the CPU oracle on this host's cores (band-parallel over row bands), on a
              bounded sample of frames;
-  clocks     SM clock samples taken by nvidia-smi during the timed region.
+  clocks     SM clock samples taken by nvidia-smi during the timed region;
+  config1, batch, inpaint2d, xbf, video, served
+             the other workloads (640x480 anaglyph; 64 mixed 720p-8K images batched and one
+             call per image; 4K with the 2-D block inpainting, and with the cross-bilateral
+             depth, each with its bound; 4K video and 8 served streams through the serving
+             loop, with latency percentiles); --quick leaves them out.
 --impl reference times the CPU oracle alone on the same workload.
 """
 import argparse
