@@ -542,13 +542,6 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    served_frames = None
-    if world == 1 and not args.quick:
-        # the served streams' moving frames, drawn on the host's cores before any GPU work
-        import multiprocessing as mp
-        sizes = [(1920, 1080)] * 4 + [(3840, 2160)] * 4
-        with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
-            served_frames = pool.map(_stream_frames, [(k, W, H, 8) for k, (W, H) in enumerate(sizes)])
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -682,7 +675,14 @@ def run_ours(args):
         extra["inpaint2d"] = bench_inpaint(D, torch, ctx, stream)
         extra["xbf"] = bench_xbf(D, torch, ctx, stream)
         extra["video"] = bench_video(D, torch, ctx)
+        # the served streams' moving frames, drawn on the host's cores (a spawned pool) only
+        # now, so that the 1.2 GB of them do not sit in host memory through the other sections
+        import multiprocessing as mp
+        sizes = [(1920, 1080)] * 4 + [(3840, 2160)] * 4
+        with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
+            served_frames = pool.map(_stream_frames, [(k, W, H, 8) for k, (W, H) in enumerate(sizes)])
         extra["served"] = bench_served(D, torch, args.served_seconds, pool_frames=served_frames)
+        del served_frames
     if rank == 0:
         peak, peak_kind = load_peaks()
         traffic, traffic_src = load_traffic()
