@@ -260,13 +260,26 @@ def bench_config1(D, torch, ctx, stream, reps=2000):
     sets = [(img.clone(), {"anaglyph": torch.empty_like(img)}) for _ in range(4)]
     p = D.make_params(max_parallax=16, outputs=("anaglyph",))
     torch.cuda.synchronize()
+    # the C-ABI call with its argument structs built once (as the main workload's loop does):
+    # at a few microseconds per frame, the binding's per-call marshalling would be the bound
+    lib = D.load()
+    keep = [(D.image_struct(i), D.outputs_struct(o)) for i, o in sets]
+    args_c = [(D.C.byref(a), D.C.byref(b)) for a, b in keep]
+    pref, h = D.C.byref(p), ctx.handle
+
+    def step(k):
+        a, b = args_c[k % 4]
+        st = lib.dibr_enqueue_image(h, a, pref, b)
+        if st != 0:
+            raise D.DibrError(st, D.dibr_last_error(h))
+
     for k in range(20):
-        ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        step(k)
     ctx.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(reps):
-        ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        step(k)
     e1.record(stream)
     ctx.synchronize()
     us = e0.elapsed_time(e1) / reps * 1000.0
@@ -274,7 +287,7 @@ def bench_config1(D, torch, ctx, stream, reps=2000):
     for k in range(50):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ctx.enqueue_image(sets[k % 4][0], p, sets[k % 4][1])
+        step(k)
         b.record(stream)
         ctx.synchronize()
         single.append(a.elapsed_time(b) * 1000.0)
