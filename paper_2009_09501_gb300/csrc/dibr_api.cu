@@ -186,6 +186,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
   return fn;
 }
 
+int dibr_ctx::band_tables(const dibr_params *p) {
+  const int32_t key[3] = {p->disparity_rule, p->max_parallax_px, p->threshold};
+  if (key[0] != args_tables_key[0] || key[1] != args_tables_key[1] || key[2] != args_tables_key[2]) {
+    shift_tables(p, args.lut_h, args.lut_n);
+    args_zguard = zguard_of(args.lut_h);
+    for (int i = 0; i < 3; ++i) args_tables_key[i] = key[i];
+  }
+  return args_zguard;
+}
+
 dibr_status dibr_ctx::plan_band(int W, int H, int depth_src, const uint8_t *in, int64_t pitch, int zguard,
                                BandArgs &a, int &smem, int &per_sm) {
   a.W = W;
@@ -346,8 +356,8 @@ dibr_status dibr_ctx::enqueue_device(const dibr_image *img, const dibr_params *p
                                                          : DS_GLOBAL;
   BandArgs &a = args;
   int smem = 0, per_sm = 1;
-  shift_tables(p, a.lut_h, a.lut_n);
-  dibr_status s = plan_band(W, H, depth_src, in, pitch, zguard_of(a.lut_h), a, smem, per_sm);
+  const int zguard = band_tables(p);
+  dibr_status s = plan_band(W, H, depth_src, in, pitch, zguard, a, smem, per_sm);
   if (s != DIBR_OK) return s;
   if ((s = encode_input(a, in, pitch)) != DIBR_OK) return s;
   Span cur_depth;  // the cross-bilateral depth this frame's band launch reads
@@ -704,8 +714,8 @@ dibr_status dibr_ctx::synthesize_banded(const dibr_image *img, const dibr_params
   BandArgs &a = args;
   int smem = 0, per_sm = 1;
   const int depth_src = p->depth_rule == DIBR_DEPTH_LUMA_BINOM5 ? DS_BINOM5 : DS_LUMA;
-  shift_tables(p, a.lut_h, a.lut_n);
-  if ((s = plan_band(W, H, depth_src, stage_in.ptr, ap, zguard_of(a.lut_h), a, smem, per_sm)) != DIBR_OK) return s;
+  const int zguard = band_tables(p);
+  if ((s = plan_band(W, H, depth_src, stage_in.ptr, ap, zguard, a, smem, per_sm)) != DIBR_OK) return s;
   if ((s = encode_input(a, stage_in.ptr, ap)) != DIBR_OK) return s;
   a.depth_in = nullptr;
   a.depth_in_pitch = 0;

@@ -57,6 +57,11 @@ struct dibr_ctx {
 
   dibr::DevBuf stage_in, stage_out, realign, xbf_depth, inpaint_scratch, inpaint_order;
   dibr::BandArgs args;  // scratch for one launch (large: keeps it off the stack)
+  // the shift tables in args (and their guard width) were built for these disparity
+  // parameters {rule, P, T}; rebuilt only when a call brings others
+  int32_t args_tables_key[3] = {-1, -1, -1};
+  int args_zguard = 0;
+  int band_tables(const dibr_params *p);  // fills args.lut_h / lut_n, returns the guard width
 
   // batched launches (dibr_batch.cu)
   dibr::DevBuf batch_desc, batch_img, batch_depth;
